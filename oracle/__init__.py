@@ -1,0 +1,24 @@
+"""Plain FP64 CPU oracle for the per-sample PEPS contraction of PEPS++.
+
+TEST INFRASTRUCTURE ONLY. Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import, call or
+run anything in this package. The product path (the CUDA library and its
+Python binding) never imports it and shares no code with it.
+
+Every function follows a passage of the paper (He et al., "PEPS++: Towards
+Extreme-scale Simulations of Strongly Correlated Quantum Many-particle Models
+on Sunway TaihuLight", arXiv:1806.03761) and says which. Where the paper is
+silent the reading taken is stated in the function's docstring.
+
+Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
+against brute-force contraction, exact diagonalisation, closed forms, finite
+differences, published Philox known-answer vectors or exact invariants, except
+that the truncated regime (D_c below the exact bond dimension) is pinned only
+through its exact special cases and invariants ("parity by same algorithm").
+"""
+from .peps import (  # noqa: F401
+    bond_list, site_tensor, BMPS, compress, upper_envs, lower_envs,
+    Strip1, Strip2, evaluate, evaluate_batch, gradient, go_step, amplitude,
+)
+from .philox import philox4x32_10, uniform53, uniform_open53  # noqa: F401
+from .sampler import init_config, metropolis_sweep, sample_chains  # noqa: F401

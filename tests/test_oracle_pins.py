@@ -1,0 +1,327 @@
+"""Pins of the FP64 oracle against things other than itself: published
+Philox known-answer vectors, brute-force contraction, exact transfer-matrix
+amplitudes, exact diagonalisation, closed forms, finite differences and
+invariants of the method (PEPS++, arXiv:1806.03761)."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import peps as op
+from synth import make_peps, random_sz0_configs
+
+from . import _exact as ex
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+# --------------------------------------------------------------------------
+# Philox4x32-10 (Salmon et al., SC'11): published known-answer vectors
+# --------------------------------------------------------------------------
+def test_philox_known_answers():
+    n = 0
+    for line in open(os.path.join(HERE, "golden", "philox4x32_10_kat.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        w = [int(x, 16) for x in line.split()]
+        assert oracle.philox4x32_10(w[0:4], w[4:6]) == tuple(w[6:10])
+        n += 1
+    assert n == 3
+
+
+def test_uniform_conversions():
+    assert oracle.uniform53(0, 0) == 0.0
+    assert oracle.uniform53(0xFFFFFFFF, 0xFFFFFFFF) == 1.0 - 2.0 ** -53
+    assert oracle.uniform_open53(0, 0) == 2.0 ** -53
+    assert oracle.uniform_open53(0xFFFFFFFF, 0xFFFFFFFF) == 1.0 - 2.0 ** -53
+
+
+# --------------------------------------------------------------------------
+# Lattice bookkeeping (Sec. "Experiment Setup")
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("L", [2, 3, 4, 7])
+def test_bond_list(L):
+    b = op.bond_list(L)
+    assert len(b) == 2 * L * (L - 1) + 2 * (L - 1) ** 2
+    ref = {(min(a, c), max(a, c)): J for a, c, J in ex.pairs(L, "J1", "J2")}
+    got = {(min(m1, m2), max(m1, m2)): ("J1" if k in "hv" else "J2") for k, m1, m2 in b}
+    assert got == ref
+
+
+# --------------------------------------------------------------------------
+# Exact contraction (Eq. PEPS): brute force and transfer matrices
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("L,D,chi", [(2, 3, 3), (3, 2, 2), (3, 3, 3), (3, 2, 8)])
+def test_amplitude_matches_brute_force(L, D, chi):
+    A = make_peps(L, D, seed=11 + L + D)
+    rng = np.random.default_rng(5)
+    for _ in range(6):
+        s = rng.integers(0, 2, L * L).astype(np.uint8)
+        la, sg = oracle.amplitude(A, s, L, chi)
+        w = ex.brute_amplitude(A, s, L)
+        assert sg == np.sign(w)
+        assert abs(la - np.log(abs(w))) < 1e-12
+
+
+def test_amplitude_4x4_all_configs_transfer_matrix():
+    L, D = 4, 2
+    A = make_peps(L, D, seed=21)
+    psi = ex.all_amplitudes(A, L)
+    rng = np.random.default_rng(7)
+    for x in rng.choice(1 << 16, 25, replace=False):
+        s = np.array([(x >> m) & 1 for m in range(16)], np.uint8)
+        la, sg = oracle.amplitude(A, s, L, 4)
+        assert sg == np.sign(psi[x])
+        assert abs(la - np.log(abs(psi[x]))) < 1e-12
+    # and the transfer matrix agrees with brute force
+    s = np.array([(12345 >> m) & 1 for m in range(16)], np.uint8)
+    assert abs(ex.brute_amplitude(A, s, L) / psi[12345] - 1) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# Local energy (Eq. ess) against exact psi and an independent H
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("J2", [0.0, 0.5, 1.0])
+def test_h_normalisation_2x2(J2):
+    # 2x2 open square = 4-site ring (+ both diagonals for J2): ground
+    # energies -2 (J2 = 0) and -3/2 (J2 = J1, complete graph: S_tot^2/2 - 3/2)
+    H = ex.dense_H(2, 1.0, J2)
+    e0 = np.linalg.eigvalsh(H)[0]
+    if J2 == 0.0:
+        assert abs(e0 + 2.0) < 1e-12
+    elif J2 == 1.0:
+        assert abs(e0 + 1.5) < 1e-12
+    psi = np.random.default_rng(0).standard_normal(16)
+    assert np.allclose(H @ psi, ex.apply_H(psi, 2, 1.0, J2))
+
+
+def test_local_energy_exact_4x4():
+    L, D = 4, 2
+    A = make_peps(L, D, seed=31)
+    psi = ex.all_amplitudes(A, L)
+    Hpsi = ex.apply_H(psi, L, 1.0, 0.5)
+    cfgs = random_sz0_configs(L, 12, seed=8)
+    for s in cfgs:
+        r = oracle.evaluate(A, s, L, 4)
+        x = ex.config_index(s)
+        e_exact = Hpsi[x] / psi[x]
+        assert abs(r["e_loc"] - e_exact) < 1e-10 * max(1.0, abs(e_exact))
+        # every flip ratio against the exact amplitudes
+        for b, (kind, m1, m2) in enumerate(op.bond_list(L)):
+            if s[m1] == s[m2]:
+                assert r["ratios"][b] == 0.0
+                continue
+            y = x ^ ((1 << m1) | (1 << m2))
+            assert abs(r["ratios"][b] - psi[y] / psi[x]) < 1e-10 * max(1.0, abs(psi[y] / psi[x]))
+        assert r["n_flips"] == sum(int(s[m1] != s[m2]) for _, m1, m2 in op.bond_list(L))
+
+
+def test_ed_identity_3x3():
+    """sum_S W^2 E(S) / sum_S W^2 = <psi|H|psi>/<psi|psi> (Eq. energy-MC)."""
+    L, D, J2 = 3, 2, 0.5
+    A = make_peps(L, D, seed=41)
+    H = ex.dense_H(L, 1.0, J2)
+    psi = np.array([ex.brute_amplitude(A, [(x >> m) & 1 for m in range(9)], L)
+                    for x in range(512)])
+    e_exact = psi @ H @ psi / (psi @ psi)
+    num = den = 0.0
+    for x in range(512):
+        s = np.array([(x >> m) & 1 for m in range(9)], np.uint8)
+        r = oracle.evaluate(A, s, L, 2, J2=J2)
+        w2 = np.exp(2 * r["log_abs"])
+        num += w2 * r["e_loc"]
+        den += w2
+    assert abs(num / den - e_exact) < 1e-11
+
+
+# --------------------------------------------------------------------------
+# D = 1 product states: closed forms
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("L,chi", [(4, 1), (5, 1), (5, 3)])
+def test_product_state_closed_form(L, chi):
+    rng = np.random.default_rng(L)
+    a = rng.uniform(0.5, 2.0, (L * L, 2)) * rng.choice([-1, 1], (L * L, 2))
+    A = a.reshape(L * L, 2, 1, 1, 1, 1)
+    s = random_sz0_configs(L, 1, seed=3)[0]
+    r = oracle.evaluate(A, s, L, chi, want_delta=True)
+    w = np.prod([a[m, s[m]] for m in range(L * L)])
+    assert abs(r["log_abs"] - np.log(abs(w))) < 1e-12 and r["sign"] == np.sign(w)
+    e = 0.0
+    for b, (kind, m1, m2) in enumerate(op.bond_list(L)):
+        J = 1.0 if kind in "hv" else 0.5
+        sg = (1 - 2 * int(s[m1])) * (1 - 2 * int(s[m2]))
+        e += J * sg / 4
+        if s[m1] != s[m2]:
+            ratio = a[m1, s[m2]] * a[m2, s[m1]] / (a[m1, s[m1]] * a[m2, s[m2]])
+            assert abs(r["ratios"][b] - ratio) < 1e-12 * abs(ratio)
+            e += J * 0.5 * ratio
+    assert abs(r["e_loc"] - e) < 1e-12 * max(1, abs(e))
+    for m in range(L * L):
+        assert abs(r["delta"][m, s[m], 0, 0, 0, 0] - 1.0 / a[m, s[m]]) < 1e-12
+        assert r["delta"][m, 1 - s[m]].max() == 0.0
+
+
+# --------------------------------------------------------------------------
+# Truncation (Fig. 1(c)): invariance once D_c reaches the exact bond
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("L,D,chis", [(4, 2, (4, 8, 16)), (6, 2, (8, 16))])
+def test_truncation_invariance(L, D, chis):
+    A = make_peps(L, D, seed=51)
+    s = random_sz0_configs(L, 1, seed=9)[0]
+    rs = [oracle.evaluate(A, s, L, c) for c in chis]
+    for r in rs[1:]:
+        assert abs(r["log_abs"] - rs[0]["log_abs"]) < 1e-10
+        assert abs(r["e_loc"] - rs[0]["e_loc"]) < 1e-10 * max(1, abs(rs[0]["e_loc"]))
+        assert np.allclose(r["ratios"], rs[0]["ratios"], rtol=1e-10, atol=1e-12)
+
+
+def test_truncation_changes_result_below_exact_bond():
+    L, D = 6, 2
+    A = make_peps(L, D, seed=51)
+    s = random_sz0_configs(L, 1, seed=9)[0]
+    exact = oracle.evaluate(A, s, L, 8)["log_abs"]
+    trunc = oracle.evaluate(A, s, L, 2)["log_abs"]
+    assert abs(exact - trunc) > 1e-8
+
+
+def test_compress_keeps_chi_largest_singular_values():
+    """A truncated two-site MPS keeps exactly the chi largest singular values
+    of its bond matrix (LAPACK SVD of the contracted pair)."""
+    rng = np.random.default_rng(3)
+    M0 = rng.standard_normal((1, 5, 7))
+    M1 = rng.standard_normal((7, 6, 1))
+    env = op.BMPS([M0, M1])
+    out = op.compress(env, 3)
+    full = np.einsum("apb,bqc->pq", M0, M1)
+    U, S, Vt = np.linalg.svd(full)
+    best = (U[:, :3] * S[:3]) @ Vt[:3]
+    got = np.einsum("apb,bqc->pq", *out.sites) * np.exp(out.logscale)
+    assert np.allclose(got, best, atol=1e-12 * S[0])
+
+
+# --------------------------------------------------------------------------
+# Log-derivatives (Eq. delta) and the gradient (Eq. gradients)
+# --------------------------------------------------------------------------
+def test_delta_finite_difference():
+    L, D = 3, 2
+    A = make_peps(L, D, seed=61)
+    s = np.array([0, 1, 0, 1, 1, 0, 0, 1, 1], np.uint8)
+    r = oracle.evaluate(A, s, L, 8, want_delta=True)
+    w0 = ex.brute_amplitude(A, s, L)
+    rng = np.random.default_rng(1)
+    h = 1e-6
+    for _ in range(12):
+        m = rng.integers(0, 9)
+        idx = (m, s[m]) + tuple(rng.integers(0, D, 4))
+        Ap, Am = A.copy(), A.copy()
+        Ap[idx] += h
+        Am[idx] -= h
+        fd = (ex.brute_amplitude(Ap, s, L) - ex.brute_amplitude(Am, s, L)) / (2 * h * w0)
+        assert abs(r["delta"][idx] - fd) < 1e-7 * max(1, abs(fd))
+
+
+@pytest.mark.parametrize("L,D,chi", [(4, 3, 4), (6, 3, 4)])
+def test_linearity_sum_T_delta_is_one(L, D, chi):
+    """sum_{lrud} A^{s_m} Delta^{s_m} = 1 per site, also under truncation:
+    B_m is the strip contracted without site m, W_i the strip itself."""
+    A = make_peps(L, D, seed=71)
+    s = random_sz0_configs(L, 1, seed=4)[0]
+    r = oracle.evaluate(A, s, L, chi, want_delta=True, want_energy=False)
+    for m in range(L * L):
+        v = np.sum(A[m, s[m]] * r["delta"][m, s[m]])
+        assert abs(v - 1.0) < 1e-10
+
+
+def test_gradient_matches_finite_difference_3x3():
+    """Exact-weight version of Eq. gradients against central differences of
+    E(A) = <psi|H|psi>/<psi|psi>, both over all 2^9 configurations."""
+    L, D, J2 = 3, 2, 0.5
+    A = make_peps(L, D, seed=81)
+    H = ex.dense_H(L, 1.0, J2)
+    confs = [np.array([(x >> m) & 1 for m in range(9)], np.uint8) for x in range(512)]
+    res = [oracle.evaluate(A, s, L, 8, J2=J2, want_delta=True) for s in confs]
+    w2 = np.array([np.exp(2 * r["log_abs"]) for r in res])
+    p = w2 / w2.sum()
+    E = np.array([r["e_loc"] for r in res])
+    sd = sum(pi * r["delta"] for pi, r in zip(p, res))
+    sde = sum(pi * r["delta"] * e for pi, r, e in zip(p, res, E))
+    g = oracle.gradient(sd, sde, float(p @ E), 1.0)
+
+    def energy(Ax):
+        psi = np.array([ex.brute_amplitude(Ax, s, L) for s in confs])
+        return psi @ H @ psi / (psi @ psi)
+
+    rng = np.random.default_rng(2)
+    h = 1e-5
+    for _ in range(5):
+        idx = (rng.integers(0, 9), rng.integers(0, 2)) + tuple(rng.integers(0, D, 4))
+        Ap, Am = A.copy(), A.copy()
+        Ap[idx] += h
+        Am[idx] -= h
+        fd = (energy(Ap) - energy(Am)) / (2 * h)
+        assert abs(g[idx] - fd) < 1e-6 * max(1.0, abs(fd))
+
+
+def test_go_step_sign_update():
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((4, 2, 1, 1, 1, 1))
+    g = rng.standard_normal(A.shape)
+    g.reshape(-1)[3] = 0.0
+    dt = 0.1
+    An = oracle.go_step(A, g, dt, seed=123, step=7)
+    d = (An - A).reshape(-1)
+    gf = g.reshape(-1)
+    assert d[3] == 0.0
+    for k in range(d.size):
+        if gf[k] != 0:
+            assert np.sign(d[k]) == -np.sign(gf[k]) and 0 < abs(d[k]) < dt
+            w = oracle.philox4x32_10((k, 0, 7, 2), (123, 0))
+            p = oracle.uniform_open53(w[0], w[1])
+            assert An.reshape(-1)[k] == A.reshape(-1)[k] - p * dt * np.sign(gf[k])
+
+
+# --------------------------------------------------------------------------
+# Metropolis sampling (Fig. "contraction", Steps 1-3; Eq. energy-MC)
+# --------------------------------------------------------------------------
+def test_init_config_is_sz0_permutation():
+    for c in range(5):
+        s = oracle.init_config(4, 99, c)
+        assert s.sum() == 8 and s.dtype == np.uint8
+    assert not np.array_equal(oracle.init_config(4, 99, 0), oracle.init_config(4, 99, 1))
+
+
+def test_sampler_stationary_distribution_2x2():
+    """Long chains on 2x2 visit the six S^z = 0 states with frequency
+    W(S)^2 / Z (W by brute force)."""
+    L, D = 2, 2
+    A = make_peps(L, D, seed=91)
+    out, final, acc = oracle.sample_chains(A, L, 4, seed=5, n_chains=4, n_burn=5,
+                                           n_thin=1, samples_per_chain=1500)
+    assert (out.sum(axis=1) == 2).all()
+    idx = np.array([ex.config_index(s) for s in out])
+    states = sorted(set(x for x in range(16) if bin(x).count("1") == 2))
+    w2 = np.array([ex.brute_amplitude(A, [(x >> m) & 1 for m in range(4)], L) ** 2 for x in states])
+    p = w2 / w2.sum()
+    f = np.array([(idx == x).mean() for x in states])
+    # 6000 correlated draws: allow 5 sigma of a binomial with a factor 2
+    sig = np.sqrt(p * (1 - p) / out.shape[0]) * 2
+    assert (np.abs(f - p) < 5 * sig + 1e-3).all()
+
+
+@pytest.mark.slow
+def test_mc_energy_4x4_within_error_bars():
+    """The MC estimate of Eq. energy-MC lies within 4 binned sigma of the
+    exact energy of the S^z = 0 projected state."""
+    L, D = 4, 2
+    A = make_peps(L, D, seed=1)
+    psi = ex.all_amplitudes(A, L)
+    sz0 = np.array([bin(x).count("1") == 8 for x in range(1 << 16)])
+    pp = np.where(sz0, psi, 0.0)
+    e_exact = pp @ ex.apply_H(pp, L, 1.0, 0.5) / (pp @ pp)
+    out, _, _ = oracle.sample_chains(A, L, 16, seed=3, n_chains=4, n_burn=10,
+                                     n_thin=1, samples_per_chain=40)
+    E = np.array([oracle.evaluate(A, s, L, 16)["e_loc"] for s in out])
+    means = E.reshape(4, -1).mean(axis=1)
+    sig = means.std(ddof=1) / np.sqrt(4)
+    assert abs(E.mean() - e_exact) < 4 * sig + 1e-9
