@@ -1,0 +1,190 @@
+/*
+ * peps.h -- C ABI of the GB300 (sm_103a) per-sample PEPS contraction library
+ * (libpeps.so): the data-parallel hot path of PEPS++ (He et al.,
+ * arXiv:1806.03761) for the open-boundary J1-J2 spin-1/2 model.
+ *
+ * For every sampled spin configuration S the library contracts the
+ * single-layer network a PEPS forms once each site's physical index is fixed
+ * (Eq. PEPS; Fig. 1(b)), row by row as a boundary MPS truncated to bond D_c
+ * (Fig. 1(c); Sec. "PEPS++ Algorithm"), and reuses the cached upper, lower,
+ * left and right environments (Fig. "contraction", Step 4) for the amplitude
+ * W(S), every J1 and J2 flip ratio of the local energy E(S) (Eq. ess), the
+ * log-derivatives Delta = dlnW/dA (Eq. delta) and their sums for the energy
+ * gradient (Eq. gradients), and for the sign-gradient update of the GO step.
+ *
+ * Conventions (every entry point):
+ *   - L x L open square lattice, N = L*L sites, site m = i*L + j, row 0 on top.
+ *   - Site tensors A: float64[N][2][D][D][D][D], axes (s, l, r, u, d), C order.
+ *     Outward legs of boundary sites use index 0 only (open boundary).
+ *   - Spins: uint8[B][N], s = 0 spin up (sigma = +1), s = 1 spin down.
+ *   - Canonical bond order (n_bonds = 2L(L-1) + 2(L-1)^2): horizontal J1
+ *     (i,j)-(i,j+1) row-major; vertical J1 (i,j)-(i+1,j); diagonal J2
+ *     (i,j)-(i+1,j+1); anti-diagonal J2 (i,j+1)-(i+1,j).
+ *   - All array arguments are DEVICE pointers owned by the caller, unless a
+ *     comment says "host".  The library owns its workspace (environments,
+ *     scratch) inside the opaque context.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls only
+ *     enqueue work on it and return; results are ready when the stream is.
+ *   - Return value: PEPS_OK or a negative PEPS_E* code; peps_last_error()
+ *     gives a message.  No C++ exception crosses this ABI.  Errors found on the
+ *     device (non-finite input, zero amplitude, a Jacobi sweep limit) are
+ *     recorded in the context and returned by peps_sync_status().
+ *   - One context per host thread at a time; calls on one context must not
+ *     overlap on the device (they share the context's workspace).
+ */
+#ifndef PEPS_GB300_H
+#define PEPS_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  PEPS_OK = 0,
+  PEPS_EINVAL = -1,   /* bad argument (NULL, size, alignment, shape) */
+  PEPS_ENOMEM = -2,   /* device allocation failed */
+  PEPS_ECUDA = -3,    /* CUDA runtime error (launch, copy, no device) */
+  PEPS_ENUMERIC = -4, /* non-finite input, zero amplitude, no convergence */
+  PEPS_ETIMEOUT = -5  /* a bounded device wait ran out */
+};
+
+enum {
+  PEPS_FP64 = 0,  /* every contraction and factorisation in FP64 */
+  PEPS_MIXED = 1  /* tensors and factorisations in float-float (two FP32,
+                     about 48 significand bits) on the FP32 pipes; ratios,
+                     energies, log-scales and gradient sums in FP64 */
+};
+
+/* Device-side error bits reported by peps_sync_status() through *flags. */
+enum {
+  PEPS_FLAG_NONFINITE = 1,   /* NaN/Inf met in a tensor or ratio */
+  PEPS_FLAG_ZERO_AMP = 2,    /* W(S) = 0 for some sample (its sign is 0) */
+  PEPS_FLAG_NO_CONVERGE = 4  /* a Jacobi SVD hit its sweep limit */
+};
+
+typedef struct peps_ctx peps_ctx;
+
+typedef struct {
+  int32_t L;          /* lattice side, 2 <= L <= 32 */
+  int32_t D;          /* PEPS bond dimension, 1 <= D <= 8 */
+  int32_t Dc;         /* boundary-MPS truncation D_c, 1 <= Dc, Dc*D <= 256 */
+  double J1, J2;      /* couplings of the J1-J2 Hamiltonian (Sec. Experiment
+                         Setup; the paper sets J1 = 1) */
+  int32_t precision;  /* PEPS_FP64 or PEPS_MIXED */
+} peps_shape;
+
+/* Create a context on the current CUDA device.  workspace_slots = number of
+ * samples processed concurrently (0 = 2 per SM); the workspace
+ * (about slots x 8 (L*L*Dc*D*Dc + ...) bytes, see peps_workspace_bytes) is
+ * allocated here with cudaMalloc.  EINVAL on a bad shape, ENOMEM if the
+ * workspace does not fit. */
+int peps_create(const peps_shape* shape, int32_t workspace_slots,
+                peps_ctx** out);
+int peps_destroy(peps_ctx* ctx);
+const char* peps_last_error(const peps_ctx* ctx);
+/* Bytes of device workspace a context with this shape and slot count holds
+ * (host call, no allocation). */
+size_t peps_workspace_bytes(const peps_shape* shape, int32_t workspace_slots);
+
+/* Copy the site tensors A (float64[N][2][D^4], device) into the context
+ * (converting to the context's precision).  Must precede every evaluation.
+ * The caller may free or change A after the stream reaches this call. */
+int peps_set_tensors(peps_ctx* ctx, const double* A, void* stream);
+
+/* W(S) for B configurations (Eq. PEPS; Fig. 1(b,c)): the lower environments
+ * Dn_{L-1} .. Dn_1 are built by boundary-MPS absorption and truncation, and
+ * the row-0 strip is closed against Dn_1.  Outputs log|W| (float64[B]) and
+ * sign (int8[B], 0 for a zero amplitude). */
+int peps_amplitudes(peps_ctx* ctx, const uint8_t* spins, int64_t B,
+                    double* log_abs, int8_t* sign, void* stream);
+
+/* Local energy E(S) of Eq. ess for B configurations: the total (not per
+ * site) sum over all J1 and J2 bonds of J [sigma_i sigma_j / 4 + (for an
+ * antiparallel pair) W(S')/W(S) / 2], each ratio taken on the one-row strip
+ * (horizontal bonds) or two-row strip (vertical and J2 bonds) between the
+ * cached upper and lower environments.  Outputs: e_loc float64[B]; log_abs
+ * float64[B] and sign int8[B] as peps_amplitudes; ratios (nullable)
+ * float64[B][n_bonds] in canonical bond order, 0 for parallel pairs;
+ * n_flips (nullable) int32[B], the number of antiparallel pairs. */
+int peps_local_energy(peps_ctx* ctx, const uint8_t* spins, int64_t B,
+                      double* e_loc, double* log_abs, int8_t* sign,
+                      double* ratios, int32_t* n_flips, void* stream);
+
+/* Log-derivatives Delta^{s_m}_{lrud}(S) = B^{s_m}_{lrud}(S) / W(S) of
+ * Eq. delta, B taken from the one-row strip of site m's row, and their sums
+ * over the batch for Eq. gradients:
+ *   sum_delta[m][s][k]   (+)= sum_b [s_b,m == s] Delta_b[m][k]
+ *   sum_delta_e[m][s][k] (+)= sum_b [s_b,m == s] Delta_b[m][k] * e_loc[b]
+ *   sum_e[0]             (+)= sum_b e_loc[b]
+ * with k = ((l*D + r)*D + u)*D + d.  e_loc: float64[B] (input, e.g. from
+ * peps_local_energy).  delta (nullable): float64[B][N][D^4], the s_m slice
+ * only.  sum_delta, sum_delta_e: float64[N][2][D^4]; sum_e: float64[1].
+ * accumulate = 0 overwrites the sums, 1 adds to them.  Sums are formed in a
+ * fixed order (bit-reproducible for a fixed slot count). */
+int peps_logderiv(peps_ctx* ctx, const uint8_t* spins, int64_t B,
+                  const double* e_loc, double* delta, double* sum_delta,
+                  double* sum_delta_e, double* sum_e, int32_t accumulate,
+                  void* stream);
+
+/* peps_local_energy and peps_logderiv in one pass over the batch (the
+ * environments are built once); the sums use the e_loc computed here.
+ * Any of ratios, n_flips, delta may be NULL. */
+int peps_evaluate(peps_ctx* ctx, const uint8_t* spins, int64_t B,
+                  double* e_loc, double* log_abs, int8_t* sign,
+                  double* ratios, int32_t* n_flips, double* delta,
+                  double* sum_delta, double* sum_delta_e, double* sum_e,
+                  int32_t accumulate, void* stream);
+
+/* One GO step (the sign update after Eq. delta, with the gradient of
+ * Eq. gradients):
+ *   g = 2 sum_delta_e / M - 2 (sum_delta / M) (sum_e[0] / M)
+ *   A[e] -= p_e * dt * sign(g[e]),   sign(0) = 0,
+ * p_e in (0,1) from Philox4x32-10 with key = seed and counter
+ * (e mod 2^32, e >> 32, step, 2): p = ((x >> 12) + 1/2) 2^-52, x the 64-bit
+ * word out[1]:out[0].  A_inout: float64[N][2][D^4] (device, updated in
+ * place); also refreshes the context's copy of the tensors.  step < 2^32. */
+int peps_grad_step(peps_ctx* ctx, const double* sum_delta,
+                   const double* sum_delta_e, const double* sum_e, int64_t M,
+                   double dt, uint64_t seed, uint64_t step, double* A_inout,
+                   void* stream);
+
+/* Metropolis sampling with weight W(S)^2 (Fig. "contraction", Steps 1-3;
+ * Eq. energy-MC) of chains chain_offset .. chain_offset+n_chains-1.
+ * Moves: exchanges of antiparallel nearest-neighbour spins (S^z kept).  A
+ * chain starts from chain_state (uint8[n_chains][N]) if non-NULL, else from
+ * a Fisher-Yates shuffle of floor(N/2) up spins (Philox key seed, counter
+ * (k, 0, chain, 0), j = x mod (k+1)).  A sweep rebuilds the lower
+ * environments and visits row i = 0..L-1: horizontal bonds left to right on
+ * the one-row strip, then vertical bonds (i,j)-(i+1,j) on the two-row strip,
+ * then absorbs row i into the upper environment.  Bond b in sweep t draws
+ * u = (x >> 11) 2^-53 from counter (b, t, chain, 1) and accepts iff
+ * u < (W(S')/W(S))^2.  Sweeps of this call are numbered first_sweep,
+ * first_sweep+1, ...; the configuration after the call's sweep number
+ * n (n = 1, 2, ...) is recorded when n > n_burn and (n - n_burn) % n_thin
+ * == 0.  spins_out: uint8[n_chains * samples_per_chain][N], chain-major.
+ * chain_state (nullable) receives the final configurations.  accepted
+ * (nullable): int64[n_chains] accepted moves. */
+int peps_sample_batch(peps_ctx* ctx, uint64_t seed, int64_t n_chains,
+                      int64_t chain_offset, int32_t n_burn, int32_t n_thin,
+                      int32_t samples_per_chain, uint64_t first_sweep,
+                      uint8_t* spins_out, uint8_t* chain_state,
+                      int64_t* accepted, void* stream);
+
+/* Wait for `stream` and return the device-side error state: PEPS_OK, or
+ * PEPS_ENUMERIC with *flags (host, nullable) set to the PEPS_FLAG_* bits
+ * seen since the last call (the bits are cleared). */
+int peps_sync_status(peps_ctx* ctx, void* stream, int32_t* flags);
+
+/* Algorithmic floating-point operation count of one sample of
+ * peps_evaluate (energy + log-derivatives) under this shape, as the kernels
+ * perform it (contractions, QR, and Jacobi at `jacobi_sweeps` sweeps); host
+ * call used for roofline reporting. */
+double peps_flops_per_sample(const peps_shape* shape, double jacobi_sweeps);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PEPS_GB300_H */

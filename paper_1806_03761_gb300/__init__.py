@@ -1,0 +1,183 @@
+"""GB300 (sm_103a) per-sample PEPS contraction: the data-parallel hot path of
+PEPS++ (He et al., arXiv:1806.03761) behind the C ABI of ``include/peps.h``.
+
+This module is a thin binding: it allocates outputs with PyTorch on the
+current CUDA device, passes raw pointers and the current stream to
+``libpeps.so`` and returns the tensors.  Every step of the contraction runs in
+the library's CUDA kernels; there is no CPU path.
+"""
+import ctypes
+
+from . import _lib
+from ._lib import PEPS_FP64, PEPS_MIXED, PepsShape  # noqa: F401
+
+__all__ = ["PepsContext", "PepsError", "bond_count", "PEPS_FP64", "PEPS_MIXED",
+           "workspace_bytes", "flops_per_sample"]
+
+
+class PepsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (_lib.ERRNAMES.get(code, code), msg))
+        self.code = code
+
+
+def bond_count(L):
+    """Number of J1 + J2 bonds of the open L x L lattice."""
+    return 2 * L * (L - 1) + 2 * (L - 1) ** 2
+
+
+def _shape(L, D, Dc, J1, J2, precision):
+    prec = {"fp64": PEPS_FP64, "mixed": PEPS_MIXED}.get(precision, precision)
+    return PepsShape(int(L), int(D), int(Dc), float(J1), float(J2), int(prec))
+
+
+def workspace_bytes(L, D, Dc, precision="fp64", slots=0, J1=1.0, J2=0.5):
+    s = _shape(L, D, Dc, J1, J2, precision)
+    return int(_lib.load().peps_workspace_bytes(ctypes.byref(s), int(slots)))
+
+
+def flops_per_sample(L, D, Dc, jacobi_sweeps=8.0, precision="fp64"):
+    s = _shape(L, D, Dc, 1.0, 0.5, precision)
+    return float(_lib.load().peps_flops_per_sample(ctypes.byref(s), float(jacobi_sweeps)))
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+class PepsContext:
+    """One library context: shape, precision form and device workspace."""
+
+    def __init__(self, L, D, Dc, J1=1.0, J2=0.5, precision="fp64", slots=0):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (there is no CPU path)")
+        self.torch = torch
+        self.lib = _lib.load()
+        self.L, self.D, self.Dc = int(L), int(D), int(Dc)
+        self.N = self.L * self.L
+        self.D4 = self.D ** 4
+        self.nbonds = bond_count(self.L)
+        self.precision = precision
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self._shape = _shape(L, D, Dc, J1, J2, precision)
+        h = ctypes.c_void_p()
+        rc = self.lib.peps_create(ctypes.byref(self._shape), int(slots), ctypes.byref(h))
+        if rc != 0:
+            raise PepsError(rc, "peps_create failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.peps_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- helpers -------------------------------------------------------------
+    def _stream(self):
+        return ctypes.c_void_p(self.torch.cuda.current_stream().cuda_stream)
+
+    def _check(self, rc):
+        if rc != 0:
+            raise PepsError(rc, self.lib.peps_last_error(self.h).decode())
+
+    def _spins(self, spins):
+        t = self.torch
+        assert spins.dtype == t.uint8 and spins.is_cuda and spins.is_contiguous()
+        assert spins.dim() == 2 and spins.shape[1] == self.N
+        return spins
+
+    def _empty(self, *shape, dtype=None):
+        return self.torch.empty(*shape, dtype=dtype or self.torch.float64, device=self.device)
+
+    # -- entry points --------------------------------------------------------
+    def set_tensors(self, A):
+        t = self.torch
+        assert A.dtype == t.float64 and A.is_cuda and A.is_contiguous()
+        assert A.numel() == self.N * 2 * self.D4
+        self._check(self.lib.peps_set_tensors(self.h, _ptr(A), self._stream()))
+
+    def amplitudes(self, spins):
+        s = self._spins(spins)
+        B = s.shape[0]
+        la, sg = self._empty(B), self._empty(B, dtype=self.torch.int8)
+        self._check(self.lib.peps_amplitudes(self.h, _ptr(s), B, _ptr(la), _ptr(sg), self._stream()))
+        return la, sg
+
+    def local_energy(self, spins, ratios=False, n_flips=False):
+        s = self._spins(spins)
+        B = s.shape[0]
+        e, la = self._empty(B), self._empty(B)
+        sg = self._empty(B, dtype=self.torch.int8)
+        r = self._empty(B, self.nbonds) if ratios else None
+        nf = self._empty(B, dtype=self.torch.int32) if n_flips else None
+        self._check(self.lib.peps_local_energy(self.h, _ptr(s), B, _ptr(e), _ptr(la), _ptr(sg),
+                                               _ptr(r), _ptr(nf), self._stream()))
+        return dict(e_loc=e, log_abs=la, sign=sg, ratios=r, n_flips=nf)
+
+    def new_sums(self):
+        return (self.torch.zeros(self.N, 2, self.D4, dtype=self.torch.float64, device=self.device),
+                self.torch.zeros(self.N, 2, self.D4, dtype=self.torch.float64, device=self.device),
+                self.torch.zeros(1, dtype=self.torch.float64, device=self.device))
+
+    def logderiv(self, spins, e_loc, delta=False, sums=None, accumulate=False):
+        s = self._spins(spins)
+        B = s.shape[0]
+        sums = sums or self.new_sums()
+        d = self._empty(B, self.N, self.D4) if delta else None
+        self._check(self.lib.peps_logderiv(self.h, _ptr(s), B, _ptr(e_loc), _ptr(d),
+                                           _ptr(sums[0]), _ptr(sums[1]), _ptr(sums[2]),
+                                           int(bool(accumulate)), self._stream()))
+        return dict(delta=d, sum_delta=sums[0], sum_delta_e=sums[1], sum_e=sums[2])
+
+    def evaluate(self, spins, ratios=False, n_flips=False, delta=False, sums=None,
+                 accumulate=False, out=None):
+        """Local energy and log-derivative sums in one pass (peps_evaluate)."""
+        s = self._spins(spins)
+        B = s.shape[0]
+        sums = sums or self.new_sums()
+        if out is None:
+            out = dict(e_loc=self._empty(B), log_abs=self._empty(B),
+                       sign=self._empty(B, dtype=self.torch.int8))
+        r = self._empty(B, self.nbonds) if ratios else None
+        nf = self._empty(B, dtype=self.torch.int32) if n_flips else None
+        d = self._empty(B, self.N, self.D4) if delta else None
+        self._check(self.lib.peps_evaluate(
+            self.h, _ptr(s), B, _ptr(out["e_loc"]), _ptr(out["log_abs"]), _ptr(out["sign"]),
+            _ptr(r), _ptr(nf), _ptr(d), _ptr(sums[0]), _ptr(sums[1]), _ptr(sums[2]),
+            int(bool(accumulate)), self._stream()))
+        res = dict(out)
+        res.update(ratios=r, n_flips=nf, delta=d, sum_delta=sums[0], sum_delta_e=sums[1],
+                   sum_e=sums[2])
+        return res
+
+    def grad_step(self, sums, M, dt, seed, step, A):
+        self._check(self.lib.peps_grad_step(self.h, _ptr(sums[0]), _ptr(sums[1]), _ptr(sums[2]),
+                                            int(M), float(dt), int(seed), int(step), _ptr(A),
+                                            self._stream()))
+        return A
+
+    def sample(self, seed, n_chains, n_burn, n_thin, samples_per_chain, chain_offset=0,
+               first_sweep=1, state=None, accepted=False):
+        t = self.torch
+        out = self._empty(n_chains * samples_per_chain, self.N, dtype=t.uint8)
+        acc = self._empty(n_chains, dtype=t.int64) if accepted else None
+        if state is not None:
+            assert state.dtype == t.uint8 and state.is_cuda and state.shape == (n_chains, self.N)
+        self._check(self.lib.peps_sample_batch(self.h, int(seed), int(n_chains), int(chain_offset),
+                                               int(n_burn), int(n_thin), int(samples_per_chain),
+                                               int(first_sweep), _ptr(out), _ptr(state), _ptr(acc),
+                                               self._stream()))
+        return (out, acc) if accepted else out
+
+    def sync_status(self):
+        f = ctypes.c_int32(0)
+        rc = self.lib.peps_sync_status(self.h, self._stream(), ctypes.byref(f))
+        if rc not in (0, _lib.PEPS_ENUMERIC):
+            self._check(rc)
+        return rc, f.value

@@ -1,0 +1,78 @@
+"""ctypes declarations of libpeps.so (include/peps.h).
+
+Argument marshalling only: every computation happens in the library's CUDA
+kernels.  Loading fails loudly when the library has not been built."""
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libpeps.so")
+
+PEPS_OK = 0
+PEPS_EINVAL = -1
+PEPS_ENOMEM = -2
+PEPS_ECUDA = -3
+PEPS_ENUMERIC = -4
+PEPS_ETIMEOUT = -5
+PEPS_FP64 = 0
+PEPS_MIXED = 1
+
+ERRNAMES = {0: "PEPS_OK", -1: "PEPS_EINVAL", -2: "PEPS_ENOMEM", -3: "PEPS_ECUDA",
+            -4: "PEPS_ENUMERIC", -5: "PEPS_ETIMEOUT"}
+
+# every entry point include/peps.h declares
+EXPORTS = ("peps_create", "peps_destroy", "peps_last_error", "peps_workspace_bytes",
+           "peps_set_tensors", "peps_amplitudes", "peps_local_energy", "peps_logderiv",
+           "peps_evaluate", "peps_grad_step", "peps_sample_batch", "peps_sync_status",
+           "peps_flops_per_sample")
+
+
+class PepsShape(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int32), ("D", ctypes.c_int32), ("Dc", ctypes.c_int32),
+                ("J1", ctypes.c_double), ("J2", ctypes.c_double),
+                ("precision", ctypes.c_int32)]
+
+
+_lib = None
+
+P = ctypes.c_void_p
+I32 = ctypes.c_int32
+I64 = ctypes.c_int64
+U64 = ctypes.c_uint64
+F64 = ctypes.c_double
+
+_SIGS = {
+    "peps_create": (I32, [ctypes.POINTER(PepsShape), I32, ctypes.POINTER(P)]),
+    "peps_destroy": (I32, [P]),
+    "peps_last_error": (ctypes.c_char_p, [P]),
+    "peps_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(PepsShape), I32]),
+    "peps_set_tensors": (I32, [P, P, P]),
+    "peps_amplitudes": (I32, [P, P, I64, P, P, P]),
+    "peps_local_energy": (I32, [P, P, I64, P, P, P, P, P, P]),
+    "peps_logderiv": (I32, [P, P, I64, P, P, P, P, P, I32, P]),
+    "peps_evaluate": (I32, [P, P, I64, P, P, P, P, P, P, P, P, P, I32, P]),
+    "peps_grad_step": (I32, [P, P, P, P, I64, F64, U64, U64, P, P]),
+    "peps_sample_batch": (I32, [P, U64, I64, I64, I32, I32, I32, U64, P, P, P, P]),
+    "peps_sync_status": (I32, [P, P, ctypes.POINTER(I32)]),
+    "peps_flops_per_sample": (F64, [ctypes.POINTER(PepsShape), F64]),
+}
+
+
+def load(path=None):
+    """Load libpeps.so (once) and declare its signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(
+            "libpeps.so not found at %s: build it with "
+            "`python -c 'import __graft_entry__ as g; g.build()'` "
+            "(there is no CPU fallback)" % path)
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib

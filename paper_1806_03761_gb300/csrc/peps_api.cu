@@ -1,0 +1,477 @@
+// peps_api.cu -- the C ABI of libpeps.so (declared in include/peps.h):
+// context and workspace management, argument checks, kernel launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/peps.h"
+#include "peps_args.h"
+#include "peps_launch.h"
+
+struct peps_ctx {
+  peps_shape shape;
+  PepsPlan plan;
+  std::vector<PepsStep> steps_h;
+  PepsStep* steps = nullptr;
+  void* As = nullptr;      // site tensors in the form's type
+  void* ws = nullptr;      // slot workspaces
+  double* wsd = nullptr;   // slot double workspaces
+  double* psum = nullptr;  // slot partial sums
+  int* flags = nullptr;
+  int nslots = 0;
+  int tensors_set = 0;
+  int device = 0;
+  std::string err;
+};
+
+namespace {
+
+int fail(peps_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+int cuda_fail(peps_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, PEPS_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+bool shape_ok(const peps_shape* s, std::string* why) {
+  if (!s) { *why = "shape is NULL"; return false; }
+  if (s->L < 2 || s->L > PEPS_MAXL) { *why = "L must be in [2, 32]"; return false; }
+  if (s->D < 1 || s->D > 8) { *why = "D must be in [1, 8]"; return false; }
+  if (s->Dc < 1 || s->Dc * s->D > 256) { *why = "Dc must be >= 1 with Dc*D <= 256"; return false; }
+  if (s->precision != PEPS_FP64 && s->precision != PEPS_MIXED) { *why = "precision must be PEPS_FP64 or PEPS_MIXED"; return false; }
+  if (!std::isfinite(s->J1) || !std::isfinite(s->J2)) { *why = "J1, J2 must be finite"; return false; }
+  return true;
+}
+
+cudaError_t launch_eval_form(const EvalArgs<double>& a, int g, cudaStream_t s) { return peps_launch_eval_f64(a, g, s); }
+cudaError_t launch_eval_form(const EvalArgs<ff>& a, int g, cudaStream_t s) { return peps_launch_eval_ff(a, g, s); }
+cudaError_t launch_sample_form(const SampleArgs<double>& a, int g, cudaStream_t s) { return peps_launch_sample_f64(a, g, s); }
+cudaError_t launch_sample_form(const SampleArgs<ff>& a, int g, cudaStream_t s) { return peps_launch_sample_ff(a, g, s); }
+
+int64_t up32(int64_t x) { return (x + 31) & ~int64_t(31); }
+
+// Bond dimensions of every absorption step (see peps_plan.h).
+void make_plan(const peps_shape& s, int nslots, PepsPlan* P, std::vector<PepsStep>* steps) {
+  const int L = s.L, D = s.D, Dc = s.Dc;
+  std::memset(P, 0, sizeof(*P));
+  P->L = L; P->D = D; P->Dc = Dc; P->N = L * L;
+  P->D2 = D * D; P->D3 = D * D * D; P->D4 = D * D * D * D;
+  P->nbonds = 2 * L * (L - 1) + 2 * (L - 1) * (L - 1);
+  P->J1 = s.J1; P->J2 = s.J2;
+  P->nsteps = L - 1;
+  steps->assign(L - 1, PepsStep());
+  for (int t = 0; t < L - 1; ++t) {
+    PepsStep& st = (*steps)[t];
+    std::memset(&st, 0, sizeof(st));
+    for (int j = 0; j < L; ++j) {
+      if (t == 0) { st.ia[j] = 1; st.ip[j] = 1; st.ib[j] = 1; }
+      else { st.ia[j] = (*steps)[t - 1].oa[j]; st.ip[j] = D; st.ib[j] = (*steps)[t - 1].ob[j]; }
+    }
+    const int Q = D;
+    int rprev = 1;
+    for (int j = 0; j < L - 1; ++j) {
+      int Bj = st.ib[j] * ((j == L - 1) ? 1 : D);
+      int r = std::min(rprev * Q, Bj);
+      st.r[j] = (int16_t)r;
+      rprev = r;
+    }
+    int cn = 1;
+    for (int j = L - 1; j >= 1; --j) {
+      int k = std::min(Dc, std::min((int)st.r[j - 1], Q * cn));
+      st.oa[j] = (int16_t)k;
+      st.ob[j] = (int16_t)cn;
+      cn = k;
+    }
+    st.oa[0] = 1;
+    st.ob[0] = (int16_t)cn;
+  }
+  P->site_cap = (int64_t)Dc * D * Dc;
+  P->env_cap = (int64_t)L * P->site_cap;
+  P->big_cap = (int64_t)Dc * Dc * D * D * D;
+  P->mat_cap = (int64_t)(Dc * D) * (Dc * D);
+  P->env2_cap = (int64_t)Dc * D * D * Dc;
+  int64_t o = 0;
+  auto take = [&](int64_t n) { int64_t r = o; o += up32(n); return r; };
+  P->off_dn = take((int64_t)(L + 1) * P->env_cap);
+  P->off_up = take(3 * P->env_cap);
+  P->off_rst = take((int64_t)L * P->mat_cap);
+  P->off_b0 = take(P->big_cap);
+  P->off_b1 = take(P->big_cap);
+  P->off_b2 = take(P->big_cap);
+  P->off_y = take(P->mat_cap);
+  P->off_xj = take(P->mat_cap);
+  P->off_vt = take(std::max<int64_t>(P->site_cap, P->D4));
+  P->off_c0 = take(P->site_cap);
+  P->off_c1 = take(P->site_cap);
+  P->off_l1 = take((int64_t)(L + 1) * P->site_cap);
+  P->off_r1 = take((int64_t)(L + 1) * P->site_cap);
+  P->off_l2 = take((int64_t)(L + 1) * P->env2_cap);
+  P->off_r2 = take((int64_t)(L + 1) * P->env2_cap);
+  P->off_tmp = take(32);
+  P->slot_elems = o;
+  int64_t d = 0;
+  auto taked = [&](int64_t n) { int64_t r = d; d += up32(n); return r; };
+  P->doff_scale = taked(4 * (L + 1));
+  P->doff_delta = taked((int64_t)P->N * P->D4);
+  P->doff_alpha = taked((int64_t)Dc * D + 8);
+  P->slot_doubles = d;
+  (void)nslots;
+}
+
+int64_t psum_len(const PepsPlan& P) { return 2 * (int64_t)P.N * 2 * P.D4 + 1; }
+
+size_t elem_size(int precision) { return precision == PEPS_FP64 ? sizeof(double) : sizeof(ff); }
+
+int default_slots() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  return 2 * sms;
+}
+
+template <class R>
+int launch_eval(peps_ctx* c, const uint8_t* spins, int64_t B, int energy, int delta_on,
+                const double* e_in, double* e_loc, double* log_abs, int8_t* sign,
+                double* ratios, int32_t* n_flips, double* delta, double* sd, double* sde,
+                double* se, int accumulate, cudaStream_t st) {
+  EvalArgs<R> a;
+  a.P = c->plan;
+  a.steps = c->steps;
+  a.As = static_cast<const R*>(c->As);
+  a.spins = spins;
+  a.B = B;
+  a.want_energy = energy;
+  a.want_delta = delta_on;
+  a.e_in = e_in;
+  a.e_loc = e_loc;
+  a.log_abs = log_abs;
+  a.sign = sign;
+  a.ratios = ratios;
+  a.n_flips = n_flips;
+  a.delta = delta;
+  a.ws = static_cast<R*>(c->ws);
+  a.wsd = c->wsd;
+  a.psum = c->psum;
+  a.flags = c->flags;
+  int grid = (int)std::min<int64_t>(c->nslots, B);
+  cudaError_t e = launch_eval_form(a, grid, st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "peps_eval_kernel launch");
+  if (delta_on) {
+    int64_t len = psum_len(c->plan);
+    e = peps_launch_reduce(c->psum, grid, len, sd, sde, se, accumulate, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "peps_reduce_slots launch");
+  }
+  return PEPS_OK;
+}
+
+int eval_common(peps_ctx* c, const uint8_t* spins, int64_t B, int energy, int delta_on,
+                const double* e_in, double* e_loc, double* log_abs, int8_t* sign,
+                double* ratios, int32_t* n_flips, double* delta, double* sd, double* sde,
+                double* se, int accumulate, void* stream) {
+  if (!c) return PEPS_EINVAL;
+  if (B < 0) return fail(c, PEPS_EINVAL, "B must be >= 0");
+  if (!c->tensors_set) return fail(c, PEPS_EINVAL, "peps_set_tensors has not been called");
+  if (B > 0 && !spins) return fail(c, PEPS_EINVAL, "spins is NULL");
+  if (delta_on && (!sd || !sde || !se)) return fail(c, PEPS_EINVAL, "sum_delta, sum_delta_e and sum_e are required");
+  if (delta_on && !energy && B > 0 && !e_in) return fail(c, PEPS_EINVAL, "e_loc is NULL");
+  if (accumulate != 0 && accumulate != 1) return fail(c, PEPS_EINVAL, "accumulate must be 0 or 1");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, PEPS_ECUDA, "cudaSetDevice failed");
+  if (B == 0) {
+    if (delta_on && !accumulate) {
+      size_t n = (size_t)c->plan.N * 2 * c->plan.D4 * sizeof(double);
+      cudaError_t e1 = cudaMemsetAsync(sd, 0, n, st);
+      cudaError_t e2 = cudaMemsetAsync(sde, 0, n, st);
+      cudaError_t e3 = cudaMemsetAsync(se, 0, sizeof(double), st);
+      if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess)
+        return fail(c, PEPS_ECUDA, "cudaMemsetAsync failed");
+    }
+    return PEPS_OK;
+  }
+  if (c->shape.precision == PEPS_FP64)
+    return launch_eval<double>(c, spins, B, energy, delta_on, e_in, e_loc, log_abs, sign, ratios,
+                               n_flips, delta, sd, sde, se, accumulate, st);
+  return launch_eval<ff>(c, spins, B, energy, delta_on, e_in, e_loc, log_abs, sign, ratios,
+                         n_flips, delta, sd, sde, se, accumulate, st);
+}
+
+
+template <class R>
+int launch_sample(peps_ctx* c, uint64_t seed, int64_t n_chains, int64_t chain_offset,
+                  int32_t n_burn, int32_t n_thin, int32_t spc, uint64_t first_sweep,
+                  uint8_t* out, uint8_t* state, int64_t* accepted, cudaStream_t st) {
+  SampleArgs<R> a;
+  a.P = c->plan;
+  a.steps = c->steps;
+  a.As = static_cast<const R*>(c->As);
+  a.k0 = (uint32_t)seed;
+  a.k1 = (uint32_t)(seed >> 32);
+  a.n_chains = n_chains;
+  a.chain_offset = chain_offset;
+  a.n_burn = n_burn;
+  a.n_thin = n_thin;
+  a.spc = spc;
+  a.first_sweep = first_sweep;
+  a.out = out;
+  a.state = state;
+  a.accepted = accepted;
+  a.ws = static_cast<R*>(c->ws);
+  a.wsd = c->wsd;
+  a.flags = c->flags;
+  int grid = (int)std::min<int64_t>(c->nslots, n_chains);
+  cudaError_t e = launch_sample_form(a, grid, st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "peps_sample_kernel launch");
+  return PEPS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t peps_workspace_bytes(const peps_shape* shape, int32_t slots) {
+  std::string why;
+  if (!shape_ok(shape, &why) || slots < 0) return 0;
+  if (slots == 0) slots = default_slots();
+  PepsPlan P;
+  std::vector<PepsStep> st;
+  make_plan(*shape, slots, &P, &st);
+  size_t es = elem_size(shape->precision);
+  return (size_t)slots * ((size_t)P.slot_elems * es + (size_t)P.slot_doubles * 8 +
+                          (size_t)psum_len(P) * 8) +
+         (size_t)P.N * 2 * P.D4 * es + st.size() * sizeof(PepsStep);
+}
+
+int peps_create(const peps_shape* shape, int32_t slots, peps_ctx** out) {
+  if (!out) return PEPS_EINVAL;
+  *out = nullptr;
+  std::string why;
+  if (!shape_ok(shape, &why)) return PEPS_EINVAL;
+  if (slots < 0) return PEPS_EINVAL;
+  peps_ctx* c = new (std::nothrow) peps_ctx();
+  if (!c) return PEPS_ENOMEM;
+  c->shape = *shape;
+  if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return PEPS_ECUDA; }
+  if (slots == 0) slots = default_slots();
+  if (slots <= 0) { delete c; return PEPS_ECUDA; }
+  c->nslots = slots;
+  make_plan(*shape, slots, &c->plan, &c->steps_h);
+  const PepsPlan& P = c->plan;
+  size_t es = elem_size(shape->precision);
+  bool ok = cudaMalloc(&c->steps, c->steps_h.size() * sizeof(PepsStep)) == cudaSuccess &&
+            cudaMalloc(&c->As, (size_t)P.N * 2 * P.D4 * es) == cudaSuccess &&
+            cudaMalloc(&c->ws, (size_t)slots * P.slot_elems * es) == cudaSuccess &&
+            cudaMalloc(&c->wsd, (size_t)slots * P.slot_doubles * 8) == cudaSuccess &&
+            cudaMalloc(&c->psum, (size_t)slots * psum_len(P) * 8) == cudaSuccess &&
+            cudaMalloc(&c->flags, sizeof(int)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    peps_destroy(c);
+    return PEPS_ENOMEM;
+  }
+  if (cudaMemcpy(c->steps, c->steps_h.data(), c->steps_h.size() * sizeof(PepsStep),
+                 cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(c->flags, 0, sizeof(int)) != cudaSuccess ||
+      cudaMemset(c->ws, 0, (size_t)slots * P.slot_elems * es) != cudaSuccess) {
+    peps_destroy(c);
+    return PEPS_ECUDA;
+  }
+  *out = c;
+  return PEPS_OK;
+}
+
+int peps_destroy(peps_ctx* c) {
+  if (!c) return PEPS_EINVAL;
+  cudaFree(c->steps);
+  cudaFree(c->As);
+  cudaFree(c->ws);
+  cudaFree(c->wsd);
+  cudaFree(c->psum);
+  cudaFree(c->flags);
+  delete c;
+  return PEPS_OK;
+}
+
+const char* peps_last_error(const peps_ctx* c) { return c ? c->err.c_str() : "no context"; }
+
+int peps_set_tensors(peps_ctx* c, const double* A, void* stream) {
+  if (!c) return PEPS_EINVAL;
+  if (!A) return fail(c, PEPS_EINVAL, "A is NULL");
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, PEPS_ECUDA, "cudaSetDevice failed");
+  int64_t n = (int64_t)c->plan.N * 2 * c->plan.D4;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = peps_launch_convert(c->shape.precision, A, c->As, n, c->flags, st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "peps_convert_kernel launch");
+  c->tensors_set = 1;
+  return PEPS_OK;
+}
+
+int peps_amplitudes(peps_ctx* c, const uint8_t* spins, int64_t B, double* log_abs,
+                    int8_t* sign, void* stream) {
+  if (c && B > 0 && (!log_abs || !sign)) return fail(c, PEPS_EINVAL, "log_abs and sign are required");
+  return eval_common(c, spins, B, 0, 0, nullptr, nullptr, log_abs, sign, nullptr, nullptr,
+                     nullptr, nullptr, nullptr, nullptr, 0, stream);
+}
+
+int peps_local_energy(peps_ctx* c, const uint8_t* spins, int64_t B, double* e_loc,
+                      double* log_abs, int8_t* sign, double* ratios, int32_t* n_flips,
+                      void* stream) {
+  if (c && B > 0 && !e_loc) return fail(c, PEPS_EINVAL, "e_loc is NULL");
+  return eval_common(c, spins, B, 1, 0, nullptr, e_loc, log_abs, sign, ratios, n_flips,
+                     nullptr, nullptr, nullptr, nullptr, 0, stream);
+}
+
+int peps_logderiv(peps_ctx* c, const uint8_t* spins, int64_t B, const double* e_loc,
+                  double* delta, double* sum_delta, double* sum_delta_e, double* sum_e,
+                  int32_t accumulate, void* stream) {
+  return eval_common(c, spins, B, 0, 1, e_loc, nullptr, nullptr, nullptr, nullptr, nullptr,
+                     delta, sum_delta, sum_delta_e, sum_e, accumulate, stream);
+}
+
+int peps_evaluate(peps_ctx* c, const uint8_t* spins, int64_t B, double* e_loc, double* log_abs,
+                  int8_t* sign, double* ratios, int32_t* n_flips, double* delta,
+                  double* sum_delta, double* sum_delta_e, double* sum_e, int32_t accumulate,
+                  void* stream) {
+  if (c && B > 0 && !e_loc) return fail(c, PEPS_EINVAL, "e_loc is NULL");
+  return eval_common(c, spins, B, 1, 1, nullptr, e_loc, log_abs, sign, ratios, n_flips, delta,
+                     sum_delta, sum_delta_e, sum_e, accumulate, stream);
+}
+
+int peps_grad_step(peps_ctx* c, const double* sum_delta, const double* sum_delta_e,
+                   const double* sum_e, int64_t M, double dt, uint64_t seed, uint64_t step,
+                   double* A_inout, void* stream) {
+  if (!c) return PEPS_EINVAL;
+  if (!sum_delta || !sum_delta_e || !sum_e || !A_inout) return fail(c, PEPS_EINVAL, "NULL argument");
+  if (M <= 0) return fail(c, PEPS_EINVAL, "M must be positive");
+  if (step >> 32) return fail(c, PEPS_EINVAL, "step must be < 2^32");
+  if (!std::isfinite(dt)) return fail(c, PEPS_EINVAL, "dt must be finite");
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, PEPS_ECUDA, "cudaSetDevice failed");
+  int64_t n = (int64_t)c->plan.N * 2 * c->plan.D4;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  cudaError_t e = peps_launch_grad(c->shape.precision, sum_delta, sum_delta_e, sum_e, (double)M, dt,
+                                   k0, k1, (uint32_t)step, A_inout, c->As, n, st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "peps_grad_kernel launch");
+  c->tensors_set = 1;
+  return PEPS_OK;
+}
+
+int peps_sample_batch(peps_ctx* c, uint64_t seed, int64_t n_chains, int64_t chain_offset,
+                      int32_t n_burn, int32_t n_thin, int32_t samples_per_chain,
+                      uint64_t first_sweep, uint8_t* spins_out, uint8_t* chain_state,
+                      int64_t* accepted, void* stream) {
+  if (!c) return PEPS_EINVAL;
+  if (n_chains < 0 || n_burn < 0 || n_thin < 1 || samples_per_chain < 0)
+    return fail(c, PEPS_EINVAL, "need n_chains >= 0, n_burn >= 0, n_thin >= 1, samples_per_chain >= 0");
+  if (chain_offset < 0 || chain_offset + n_chains > (int64_t(1) << 32))
+    return fail(c, PEPS_EINVAL, "chain indices must lie in [0, 2^32)");
+  int64_t total = (int64_t)n_burn + (int64_t)samples_per_chain * n_thin;
+  if (first_sweep + (uint64_t)total > (uint64_t(1) << 32))
+    return fail(c, PEPS_EINVAL, "sweep numbers must lie in [0, 2^32)");
+  if (n_chains > 0 && samples_per_chain > 0 && !spins_out) return fail(c, PEPS_EINVAL, "spins_out is NULL");
+  if (!c->tensors_set) return fail(c, PEPS_EINVAL, "peps_set_tensors has not been called");
+  if (n_chains == 0) return PEPS_OK;
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, PEPS_ECUDA, "cudaSetDevice failed");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (c->shape.precision == PEPS_FP64)
+    return launch_sample<double>(c, seed, n_chains, chain_offset, n_burn, n_thin, samples_per_chain,
+                                 first_sweep, spins_out, chain_state, accepted, st);
+  return launch_sample<ff>(c, seed, n_chains, chain_offset, n_burn, n_thin, samples_per_chain,
+                           first_sweep, spins_out, chain_state, accepted, st);
+}
+
+int peps_sync_status(peps_ctx* c, void* stream, int32_t* flags) {
+  if (!c) return PEPS_EINVAL;
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, PEPS_ECUDA, "cudaSetDevice failed");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
+  int h = 0;
+  e = cudaMemcpy(&h, c->flags, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "reading the error flags");
+  e = cudaMemset(c->flags, 0, sizeof(int));
+  if (e != cudaSuccess) return cuda_fail(c, e, "clearing the error flags");
+  if (flags) *flags = h;
+  if (h) return fail(c, PEPS_ENUMERIC, "device-side numeric condition (see flags)");
+  return PEPS_OK;
+}
+
+double peps_flops_per_sample(const peps_shape* shape, double jacobi_sweeps) {
+  std::string why;
+  if (!shape_ok(shape, &why)) return 0.0;
+  PepsPlan P;
+  std::vector<PepsStep> steps;
+  make_plan(*shape, 1, &P, &steps);
+  const int L = P.L, D = P.D;
+  double f = 0.0;
+  // environments: both directions, every step
+  for (int dir = 0; dir < 2; ++dir)
+    for (int t = 0; t < L - 1; ++t) {
+      if (dir == 1 && t == L - 2) continue;  // U_{L-2} is built but Dn_0 is not
+      const PepsStep& st = steps[t];
+      int rprev = 1;
+      for (int j = 0; j < L - 1; ++j) {
+        double a = st.ia[j], p = st.ip[j], b = st.ib[j];
+        double Dl = j == 0 ? 1 : D, Dr = j == L - 1 ? 1 : D;
+        double m = (double)rprev * D, n = b * Dr;
+        f += 2.0 * rprev * Dl * p * b * a;            // S1
+        f += 2.0 * rprev * D * b * Dr * Dl * p;       // X
+        double kq = std::min(m, n);
+        f += 2.0 * m * n * kq - (2.0 / 3.0) * kq * kq * kq;  // Householder R
+        rprev = st.r[j];
+      }
+      int cn = 1;
+      for (int j = L - 1; j >= 0; --j) {
+        double a = st.ia[j], p = st.ip[j], b = st.ib[j];
+        double Dl = j == 0 ? 1 : D, Dr = j == L - 1 ? 1 : D;
+        f += 2.0 * a * p * Dr * cn * b;               // S2
+        f += 2.0 * a * Dl * D * cn * p * Dr;          // Y
+        if (j == 0) break;
+        double rr = st.r[j - 1], n = (double)D * cn, A = a * Dl;
+        f += 2.0 * rr * n * A;                        // X_j = R Y
+        double r2 = std::min(rr, n);
+        if (rr > n) f += 2.0 * rr * n * n - (2.0 / 3.0) * n * n * n;
+        f += jacobi_sweeps * (r2 * (r2 - 1) / 2.0) * (2.0 * n + 6.0 * n);  // dots + rotations
+        f += 2.0 * A * st.oa[j] * n;                  // C_j
+        cn = st.oa[j];
+      }
+    }
+  // strips (interior estimate with the output dims of the environments)
+  auto ud = [&](int row, int j, int which) -> double {  // U_row dims
+    if (row < 0) return 1.0;
+    return which == 0 ? steps[row].oa[j] : steps[row].ob[j];
+  };
+  auto dd = [&](int row, int j, int which) -> double {  // Dn_row dims
+    if (row >= L) return 1.0;
+    int t = L - 1 - row;
+    return which == 0 ? steps[t].oa[j] : steps[t].ob[j];
+  };
+  for (int i = 0; i < L; ++i) {
+    double pu = i == 0 ? 1 : D, pd = i == L - 1 ? 1 : D;
+    for (int j = 0; j < L; ++j) {
+      double Dl = j == 0 ? 1 : D, Dr = j == L - 1 ? 1 : D;
+      double au = ud(i - 1, j, 0), bu = ud(i - 1, j, 1), ad = dd(i + 1, j, 0), bd = dd(i + 1, j, 1);
+      double step1 = 2 * Dl * ad * pu * bu * au + 2 * ad * bu * Dr * pd * Dl * pu + 2 * bu * Dr * bd * ad * pd;
+      f += 2 * step1;                                        // left + right envs
+      f += 2 * Dl * ad * pu * bu * au + 2 * bu * Dr * ad * pd * bd + 2 * Dl * Dr * pu * pd * ad * bu;  // B
+      if (j + 1 < L) f += 0.5 * 2 * step1;                   // half the horizontal pairs flip (2 steps)
+      if (i + 1 < L) {
+        double pd2 = i + 1 == L - 1 ? 1 : D;
+        double ad2 = dd(i + 2, j, 0), bd2 = dd(i + 2, j, 1);
+        double s2 = 2 * Dl * Dl * ad2 * pu * bu * au + 2 * Dl * ad2 * bu * Dr * D * Dl * pu +
+                    2 * ad2 * bu * Dr * Dr * pd2 * Dl * D + 2 * bu * Dr * Dr * bd2 * ad2 * pd2;
+        f += 2 * s2;                                         // left + right envs
+        f += 0.5 * s2 + (j + 1 < L ? 0.5 * 2 * 2 * s2 : 0);  // v, d, a ratios at half filling
+      }
+    }
+  }
+  return f;
+}
+
+}  // extern "C"

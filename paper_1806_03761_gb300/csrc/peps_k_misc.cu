@@ -1,0 +1,47 @@
+// Small kernels: slot-sum reduction, tensor conversion, GO update.
+#include "peps_eval.cuh"
+#include "peps_launch.h"
+#include "../../include/peps.h"
+
+// sums[k] (+)= sum over slots of the slot partial sums (fixed order)
+__global__ void peps_reduce_slots(const double* psum, int nslots, int64_t len,
+                                  double* sd, double* sde, double* se, int accumulate) {
+  const int64_t stride = len;
+  const int64_t half = (len - 1) / 2;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < len; k += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int q = 0; q < nslots; ++q) s += psum[(int64_t)q * stride + k];
+    double* dst = (k < half) ? sd + k : (k < 2 * half ? sde + (k - half) : se);
+    *dst = accumulate ? *dst + s : s;
+  }
+}
+
+cudaError_t peps_launch_reduce(const double* psum, int nslots, int64_t len, double* sd,
+                               double* sde, double* se, int accumulate, cudaStream_t st) {
+  int rg = (int)((len + 255) / 256 < 4096 ? (len + 255) / 256 : 4096);
+  peps_reduce_slots<<<rg, 256, 0, st>>>(psum, nslots, len, sd, sde, se, accumulate);
+  return cudaGetLastError();
+}
+
+cudaError_t peps_launch_convert(int precision, const double* A, void* As, int64_t n, int* flags,
+                                cudaStream_t st) {
+  int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+  if (precision == PEPS_FP64)
+    peps_convert_kernel<double><<<grid, 256, 0, st>>>(A, static_cast<double*>(As), n, flags);
+  else
+    peps_convert_kernel<ff><<<grid, 256, 0, st>>>(A, static_cast<ff*>(As), n, flags);
+  return cudaGetLastError();
+}
+
+cudaError_t peps_launch_grad(int precision, const double* sd, const double* sde, const double* se,
+                             double M, double dt, uint32_t k0, uint32_t k1, uint32_t step,
+                             double* A, void* As, int64_t n, cudaStream_t st) {
+  int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+  if (precision == PEPS_FP64)
+    peps_grad_kernel<double><<<grid, 256, 0, st>>>(sd, sde, se, M, dt, k0, k1, step, A,
+                                                   static_cast<double*>(As), n);
+  else
+    peps_grad_kernel<ff><<<grid, 256, 0, st>>>(sd, sde, se, M, dt, k0, k1, step, A,
+                                               static_cast<ff*>(As), n);
+  return cudaGetLastError();
+}

@@ -1,0 +1,21 @@
+// peps_launch.h -- host-side launchers of the kernels, one translation unit
+// per kernel family and form so that the library compiles in parallel.
+#pragma once
+#include <cuda_runtime.h>
+#include "peps_arith.cuh"
+#include "peps_plan.h"
+
+template <class R> struct EvalArgs;
+template <class R> struct SampleArgs;
+
+cudaError_t peps_launch_eval_f64(const EvalArgs<double>& a, int grid, cudaStream_t st);
+cudaError_t peps_launch_eval_ff(const EvalArgs<ff>& a, int grid, cudaStream_t st);
+cudaError_t peps_launch_sample_f64(const SampleArgs<double>& a, int grid, cudaStream_t st);
+cudaError_t peps_launch_sample_ff(const SampleArgs<ff>& a, int grid, cudaStream_t st);
+cudaError_t peps_launch_reduce(const double* psum, int nslots, int64_t len, double* sd,
+                               double* sde, double* se, int accumulate, cudaStream_t st);
+cudaError_t peps_launch_convert(int precision, const double* A, void* As, int64_t n, int* flags,
+                                cudaStream_t st);
+cudaError_t peps_launch_grad(int precision, const double* sd, const double* sde, const double* se,
+                             double M, double dt, uint32_t k0, uint32_t k1, uint32_t step,
+                             double* A, void* As, int64_t n, cudaStream_t st);

@@ -1,0 +1,235 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle,
+element by element, on seeded synthetic inputs.
+
+Tolerances (stated in the task for this method): FP64 form 1e-10, mixed
+(float-float) form 1e-4 -- relative on E(S), on W(S) as |dlog|W|| with equal
+signs, on every flip ratio (with an absolute floor of tol * RMS of the
+sample's ratios) and on the Delta sums (relative to their largest entry).
+Integer outputs (signs, flip counts, sampled spins) must match exactly."""
+import numpy as np
+import pytest
+
+import oracle
+from synth import make_peps, random_sz0_configs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "mixed": 1e-4}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def ctx_for(L, D, Dc, prec, slots=0, J2=0.5):
+    from paper_1806_03761_gb300 import PepsContext
+    return PepsContext(L, D, Dc, J1=1.0, J2=J2, precision=prec, slots=slots)
+
+
+def check_eval(A, spins, L, D, Dc, prec, slots=0, delta=True):
+    tol = TOL[prec]
+    ctx = ctx_for(L, D, Dc, prec, slots)
+    ctx.set_tensors(torch.from_numpy(A).cuda())
+    sp = torch.from_numpy(np.ascontiguousarray(spins)).cuda()
+    res = ctx.evaluate(sp, ratios=True, n_flips=True, delta=delta)
+    rc, flags = ctx.sync_status()
+    assert rc == 0, flags
+    ref = oracle.evaluate_batch(A, spins, L, Dc, want_delta=delta)
+    la = res["log_abs"].cpu().numpy()
+    sg = res["sign"].cpu().numpy()
+    e = res["e_loc"].cpu().numpy()
+    r = res["ratios"].cpu().numpy()
+    nf = res["n_flips"].cpu().numpy()
+    assert np.array_equal(sg, ref["sign"].astype(np.int8))
+    assert np.array_equal(nf, ref["n_flips"])
+    err = dict(log_abs=np.max(np.abs(la - ref["log_abs"])),
+               e_loc=np.max(np.abs(e - ref["e_loc"]) / np.maximum(1.0, np.abs(ref["e_loc"]))))
+    for b in range(len(spins)):
+        rr = ref["ratios"][b]
+        assert np.array_equal(r[b] == 0, rr == 0)
+        m = rr != 0
+        if m.any():
+            floor = tol * np.sqrt(np.mean(rr[m] ** 2))
+            err["ratios"] = max(err.get("ratios", 0.0),
+                                np.max(np.abs(r[b][m] - rr[m]) / np.maximum(np.abs(rr[m]), floor / tol)))
+    if delta:
+        N, D4 = L * L, D ** 4
+        sd = np.zeros((N, 2, D4))
+        sde = np.zeros((N, 2, D4))
+        for b in range(len(spins)):
+            for mm in range(N):
+                dv = ref["delta"][b, mm, spins[b][mm]].reshape(-1)
+                sd[mm, spins[b][mm]] += dv
+                sde[mm, spins[b][mm]] += dv * ref["e_loc"][b]
+        gd = res["sum_delta"].cpu().numpy()
+        gde = res["sum_delta_e"].cpu().numpy()
+        err["sum_delta"] = np.max(np.abs(gd - sd)) / np.abs(sd).max()
+        err["sum_delta_e"] = np.max(np.abs(gde - sde)) / np.abs(sde).max()
+        err["sum_e"] = abs(res["sum_e"].item() - ref["e_loc"].sum()) / max(1, abs(ref["e_loc"].sum()))
+        dg = res["delta"].cpu().numpy()
+        dr = np.stack([ref["delta"][b, np.arange(N), spins[b]].reshape(N, -1) for b in range(len(spins))])
+        err["delta"] = np.max(np.abs(dg - dr)) / np.abs(dr).max()
+    print(prec, L, D, Dc, {k: "%.2e" % v for k, v in err.items()})
+    for k, v in err.items():
+        assert v <= tol, (k, v)
+    ctx.close()
+    return err
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_parity_4x4_D2_Dc16_exact_regime(prec):
+    A = make_peps(4, 2, seed=1)
+    spins = random_sz0_configs(4, 40, seed=2)
+    check_eval(A, spins, 4, 2, 16, prec)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_parity_6x6_D3_Dc4_truncated_ragged_batch(prec):
+    A = make_peps(6, 3, seed=3)
+    spins = random_sz0_configs(6, 7, seed=4)
+    check_eval(A, spins, 6, 3, 4, prec, slots=3)  # 7 samples over 3 slots
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_parity_8x8_D4_Dc16_neel(prec):
+    A = make_peps(8, 4, seed=2, kind="neel", eps=1e-2)
+    spins = random_sz0_configs(8, 10, seed=3)
+    check_eval(A, spins, 8, 4, 16, prec)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_parity_16x16_D6_Dc24(prec):
+    A = make_peps(16, 6, seed=4)
+    spins = random_sz0_configs(16, 2, seed=5)
+    check_eval(A, spins, 16, 6, 24, prec)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_amplitudes_and_logderiv_entry_points(prec):
+    L, D, Dc = 5, 2, 4
+    tol = TOL[prec]
+    A = make_peps(L, D, seed=9)
+    spins = random_sz0_configs(L, 9, seed=10)
+    ctx = ctx_for(L, D, Dc, prec)
+    ctx.set_tensors(torch.from_numpy(A).cuda())
+    sp = torch.from_numpy(spins).cuda()
+    la, sg = ctx.amplitudes(sp)
+    ref = oracle.evaluate_batch(A, spins, L, Dc, want_delta=True)
+    assert np.array_equal(sg.cpu().numpy(), ref["sign"].astype(np.int8))
+    assert np.max(np.abs(la.cpu().numpy() - ref["log_abs"])) < tol
+    le = ctx.local_energy(sp, ratios=True)
+    assert np.allclose(le["e_loc"].cpu().numpy(), ref["e_loc"], rtol=tol, atol=tol)
+    # logderiv with given energies, then accumulate a second batch
+    e_in = torch.from_numpy(ref["e_loc"]).cuda()
+    r1 = ctx.logderiv(sp, e_in, delta=True)
+    sums = (r1["sum_delta"].clone(), r1["sum_delta_e"].clone(), r1["sum_e"].clone())
+    ctx.logderiv(sp, e_in, sums=sums, accumulate=True)
+    N = L * L
+    sd = np.zeros((N, 2, D ** 4))
+    for b in range(len(spins)):
+        for m in range(N):
+            sd[m, spins[b][m]] += ref["delta"][b, m, spins[b][m]].reshape(-1)
+    got = sums[0].cpu().numpy()
+    assert np.max(np.abs(got - 2 * sd)) <= tol * np.abs(sd).max() * 2
+    assert abs(sums[2].item() - 2 * ref["e_loc"].sum()) <= tol * max(1, abs(ref["e_loc"].sum()))
+    assert ctx.sync_status()[0] == 0
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_grad_step_bit_exact(prec):
+    L, D = 4, 2
+    A = make_peps(L, D, seed=11)
+    rng = np.random.default_rng(12)
+    sd = rng.standard_normal((L * L, 2, D ** 4))
+    sde = rng.standard_normal((L * L, 2, D ** 4))
+    sd[0, 0, :3] = 0.0
+    sde[0, 0, :3] = 0.0  # g = 0 exactly: element unchanged
+    se = np.array([rng.standard_normal()])
+    M, dt, seed, step = 37, 0.05, 0xDEADBEEF12345, 9
+    ctx = ctx_for(L, D, 4, prec)
+    Ad = torch.from_numpy(A.copy()).cuda()
+    ctx.set_tensors(Ad)
+    ctx.grad_step((torch.from_numpy(sd).cuda(), torch.from_numpy(sde).cuda(), torch.from_numpy(se).cuda()),
+                  M, dt, seed, step, Ad)
+    g = oracle.gradient(sd, sde, se[0], M)
+    ref = oracle.go_step(A, g.reshape(A.shape), dt, seed, step)
+    assert np.array_equal(Ad.cpu().numpy(), ref)
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("L,D,Dc", [(4, 2, 16), (4, 3, 4)])
+def test_sampler_bit_exact(prec, L, D, Dc):
+    A = make_peps(L, D, seed=1)
+    ctx = ctx_for(L, D, Dc, prec, slots=2)
+    ctx.set_tensors(torch.from_numpy(A).cuda())
+    out, acc = ctx.sample(seed=12345678901, n_chains=3, n_burn=3, n_thin=2, samples_per_chain=3,
+                          accepted=True)
+    ref, fin, racc = oracle.sample_chains(A, L, Dc, 12345678901, 3, 3, 2, 3)
+    assert np.array_equal(out.cpu().numpy(), ref)
+    assert np.array_equal(acc.cpu().numpy(), racc)
+    # resume from the final states: the next sweeps continue the chains
+    state = torch.from_numpy(fin.copy()).cuda()
+    out2 = ctx.sample(seed=12345678901, n_chains=3, n_burn=0, n_thin=1, samples_per_chain=2,
+                      first_sweep=10, state=state)
+    ref2, fin2, _ = oracle.sample_chains(A, L, Dc, 12345678901, 3, 0, 1, 2, init=fin, first_sweep=10)
+    assert np.array_equal(out2.cpu().numpy(), ref2)
+    assert np.array_equal(state.cpu().numpy(), fin2)
+    ctx.close()
+
+
+# ---------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------
+def test_empty_batch_and_invalid_arguments():
+    from paper_1806_03761_gb300 import PepsError
+    ctx = ctx_for(4, 2, 4, "fp64")
+    ctx.set_tensors(torch.from_numpy(make_peps(4, 2, seed=1)).cuda())
+    sp = torch.zeros(0, 16, dtype=torch.uint8, device="cuda")
+    res = ctx.evaluate(sp)
+    assert res["e_loc"].numel() == 0 and float(res["sum_delta"].abs().max()) == 0.0
+    with pytest.raises(PepsError):
+        ctx.sample(seed=1, n_chains=2, n_burn=1, n_thin=0, samples_per_chain=1)
+    with pytest.raises(PepsError):
+        ctx.grad_step(ctx.new_sums(), 0, 0.1, 1, 1, torch.zeros(16, 2, 16, dtype=torch.float64, device="cuda"))
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_minimal_lattice_and_product_state(prec):
+    # L = 2 (smallest lattice) and D = 1 (product state, closed forms)
+    check_eval(make_peps(2, 2, seed=5), random_sz0_configs(2, 6, seed=6), 2, 2, 4, prec)
+    L = 5
+    rng = np.random.default_rng(3)
+    a = rng.uniform(0.5, 2.0, (L * L, 2)) * rng.choice([-1, 1], (L * L, 2))
+    check_eval(a.reshape(L * L, 2, 1, 1, 1, 1), random_sz0_configs(L, 4, seed=7), L, 1, 2, prec)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_unbalanced_configs_and_largest_bond(prec):
+    # S^z != 0 configurations (all up: no flips) and D*Dc at its maximum 256
+    L, D, Dc = 3, 8, 32
+    A = make_peps(L, D, seed=13)
+    spins = np.zeros((3, 9), np.uint8)
+    spins[1, :4] = 1
+    spins[2] = random_sz0_configs(3, 1, seed=1)[0]
+    check_eval(A, spins, L, D, Dc, prec, delta=False)
+
+
+def test_zero_amplitude_is_flagged():
+    L, D, Dc = 3, 2, 4
+    A = make_peps(L, D, seed=14)
+    A[4, 0] = 0.0  # the centre site's spin-up slice vanishes
+    spins = np.array([[0, 1, 0, 1, 0, 1, 0, 1, 0]], np.uint8)
+    ctx = ctx_for(L, D, Dc, "fp64")
+    ctx.set_tensors(torch.from_numpy(A).cuda())
+    la, sg = ctx.amplitudes(torch.from_numpy(spins).cuda())
+    rc, flags = ctx.sync_status()
+    assert sg.item() == 0 and rc != 0 and flags & 2
+    ctx.close()
