@@ -157,6 +157,37 @@ def lower_envs(A, spins, L, chi):
     return out
 
 
+# Column steps of the strips, written as pairwise tensordot contractions.
+def _left1(L, U, T, Dn):
+    """L'[B,r,D] = sum L[x,y,z] U[x,u,B] T[y,r,u,d] Dn[z,d,D]."""
+    t = np.tensordot(L, U, axes=([0], [0]))          # y z u B
+    t = np.tensordot(t, T, axes=([0, 2], [0, 2]))    # z B r d
+    return np.tensordot(t, Dn, axes=([0, 3], [0, 1]))  # B r D
+
+
+def _right1(U, T, Dn, R):
+    """R'[x,y,z] = sum U[x,u,B] T[y,r,u,d] Dn[z,d,D] R[B,r,D]."""
+    t = np.tensordot(Dn, R, axes=([2], [2]))         # z d B r
+    t = np.tensordot(T, t, axes=([1, 3], [3, 1]))    # y u z B
+    return np.tensordot(U, t, axes=([1, 2], [1, 3])).transpose(0, 1, 2)  # x y z
+
+
+def _left2(L, U, T1, T2, Dn):
+    """L'[B,r,s,D] = sum L[w,x,y,z] U[w,u,B] T1[x,r,u,m] T2[y,s,m,d] Dn[z,d,D]."""
+    t = np.tensordot(L, U, axes=([0], [0]))          # x y z u B
+    t = np.tensordot(t, T1, axes=([0, 3], [0, 2]))   # y z B r m
+    t = np.tensordot(t, T2, axes=([0, 4], [0, 2]))   # z B r s d
+    return np.tensordot(t, Dn, axes=([0, 4], [0, 1]))  # B r s D
+
+
+def _right2(U, T1, T2, Dn, R):
+    """R'[w,x,y,z] = sum U[w,u,B] T1[x,r,u,m] T2[y,s,m,d] Dn[z,d,D] R[B,r,s,D]."""
+    t = np.tensordot(Dn, R, axes=([2], [3]))         # z d B r s
+    t = np.tensordot(T2, t, axes=([1, 3], [4, 1]))   # y m z B r
+    t = np.tensordot(T1, t, axes=([1, 3], [4, 1]))   # x u y z B
+    return np.tensordot(U, t, axes=([1, 2], [1, 4]))  # w x y z
+
+
 def _unit(x):
     """Scale to unit max-abs; returns (scaled, log of the scale)."""
     s = np.abs(x).max()
@@ -179,8 +210,7 @@ class Strip1:
         self.Lenv = [np.ones((1, 1, 1))]
         self.cL = [0.0]
         for j in range(L):
-            x = np.einsum("xyz,xuB,yrud,zdD->BrD", self.Lenv[j], up.sites[j],
-                          self.T[j], dn.sites[j], optimize=True)
+            x = _left1(self.Lenv[j], up.sites[j], self.T[j], dn.sites[j])
             x, c = _unit(x)
             self.Lenv.append(x)
             self.cL.append(self.cL[-1] + c)
@@ -188,8 +218,7 @@ class Strip1:
         self.cR = [0.0] * (L + 1)
         self.Renv[L] = np.ones((1, 1, 1))
         for j in range(L - 1, -1, -1):
-            x = np.einsum("xuB,yrud,zdD,BrD->xyz", up.sites[j], self.T[j],
-                          dn.sites[j], self.Renv[j + 1], optimize=True)
+            x = _right1(up.sites[j], self.T[j], dn.sites[j], self.Renv[j + 1])
             x, c = _unit(x)
             self.Renv[j] = x
             self.cR[j] = self.cR[j + 1] + c
@@ -204,8 +233,7 @@ class Strip1:
         """Contract L_j, the columns j..j+len(Ts)-1 with tensors Ts, R_{j+k}."""
         x = self.Lenv[j]
         for k, T in enumerate(Ts):
-            x = np.einsum("xyz,xuB,yrud,zdD->BrD", x, self.up.sites[j + k], T,
-                          self.dn.sites[j + k], optimize=True)
+            x = _left1(x, self.up.sites[j + k], T, self.dn.sites[j + k])
         return float(np.einsum("xyz,xyz->", x, self.Renv[j + len(Ts)]))
 
     def ratio(self, j, new_T):
@@ -217,8 +245,11 @@ class Strip1:
     def B(self, j):
         """B^{s_m}(S) of Eq. delta for site (i, j), scaled so that dividing by
         ``scaled_value`` gives Delta: returns (B_scaled, W_scaled)."""
-        Bt = np.einsum("xyz,xuB,zdD,BrD->yrud", self.Lenv[j], self.up.sites[j],
-                       self.dn.sites[j], self.Renv[j + 1], optimize=True)
+        # B = L_j U_j Dn_j R_{j+1} with the site tensor left out
+        lu = np.tensordot(self.Lenv[j], self.up.sites[j], axes=([0], [0]))   # y z u B
+        rd = np.tensordot(self.Renv[j + 1], self.dn.sites[j], axes=([2], [2]))  # B r z d
+        Bt = np.tensordot(lu, rd, axes=([1, 3], [2, 0]))                     # y u r d
+        Bt = Bt.transpose(0, 2, 1, 3)                                        # y r u d
         v = float(self.Lenv[self.L].reshape(()))
         # Bt carries exp(-(cL[j]+cR[j+1])), v carries exp(-cL[L])
         factor = np.exp(self.cL[j] + self.cR[j + 1] - self.cL[self.L])
@@ -241,14 +272,12 @@ class Strip2:
         self.Renv = [None] * (L + 1)
         self.Renv[L] = np.ones((1, 1, 1, 1))
         for j in range(L - 1, -1, -1):
-            x = np.einsum("wuB,xrum,ysmd,zdD,BrsD->wxyz", self.up.sites[j],
-                          self.T1[j], self.T2[j], self.dn.sites[j],
-                          self.Renv[j + 1], optimize=True)
+            x = _right2(self.up.sites[j], self.T1[j], self.T2[j],
+                        self.dn.sites[j], self.Renv[j + 1])
             self.Renv[j] = _unit(x)[0]
 
     def _step_left(self, x, j, T1, T2):
-        return np.einsum("wxyz,wuB,xrum,ysmd,zdD->BrsD", x, self.up.sites[j],
-                         T1, T2, self.dn.sites[j], optimize=True)
+        return _left2(x, self.up.sites[j], T1, T2, self.dn.sites[j])
 
     def window(self, j, cols):
         x = self.Lenv[j]
