@@ -53,9 +53,14 @@ enum {
 
 enum {
   PEPS_FP64 = 0,  /* every contraction and factorisation in FP64 */
-  PEPS_MIXED = 1  /* tensors and factorisations in float-float (two FP32,
-                     about 48 significand bits) on the FP32 pipes; ratios,
-                     energies, log-scales and gradient sums in FP64 */
+  PEPS_MIXED = 1, /* tensors, contractions and the QR/SVD truncation in
+                     float-float (a pair of FP32 numbers, about 48
+                     significand bits) on the FP32 pipes; log-scales, flip
+                     ratios, energies and the Delta and gradient sums in FP64 */
+  PEPS_FP32 = 2   /* tensors, contractions and truncation in plain FP32,
+                     scalars as PEPS_MIXED.  Diagnostic form: its error grows
+                     with the cancellation in W(S) and is not held to the
+                     1e-4 tolerance */
 };
 
 /* Device-side error bits reported by peps_sync_status() through *flags. */
@@ -73,7 +78,7 @@ typedef struct {
   int32_t Dc;         /* boundary-MPS truncation D_c, 1 <= Dc, Dc*D <= 256 */
   double J1, J2;      /* couplings of the J1-J2 Hamiltonian (Sec. Experiment
                          Setup; the paper sets J1 = 1) */
-  int32_t precision;  /* PEPS_FP64 or PEPS_MIXED */
+  int32_t precision;  /* PEPS_FP64, PEPS_MIXED or PEPS_FP32 */
 } peps_shape;
 
 /* Create a context on the current CUDA device.  workspace_slots = number of

@@ -9,9 +9,9 @@ the library's CUDA kernels; there is no CPU path.
 import ctypes
 
 from . import _lib
-from ._lib import PEPS_FP64, PEPS_MIXED, PepsShape  # noqa: F401
+from ._lib import PEPS_FP32, PEPS_FP64, PEPS_MIXED, PepsShape  # noqa: F401
 
-__all__ = ["PepsContext", "PepsError", "bond_count", "PEPS_FP64", "PEPS_MIXED",
+__all__ = ["PepsContext", "PepsError", "bond_count", "PEPS_FP64", "PEPS_MIXED", "PEPS_FP32",
            "workspace_bytes", "flops_per_sample"]
 
 
@@ -27,7 +27,7 @@ def bond_count(L):
 
 
 def _shape(L, D, Dc, J1, J2, precision):
-    prec = {"fp64": PEPS_FP64, "mixed": PEPS_MIXED}.get(precision, precision)
+    prec = {"fp64": PEPS_FP64, "mixed": PEPS_MIXED, "fp32": PEPS_FP32}.get(precision, precision)
     return PepsShape(int(L), int(D), int(Dc), float(J1), float(J2), int(prec))
 
 

@@ -16,6 +16,7 @@ PEPS_ENUMERIC = -4
 PEPS_ETIMEOUT = -5
 PEPS_FP64 = 0
 PEPS_MIXED = 1
+PEPS_FP32 = 2
 
 ERRNAMES = {0: "PEPS_OK", -1: "PEPS_EINVAL", -2: "PEPS_ENOMEM", -3: "PEPS_ECUDA",
             -4: "PEPS_ENUMERIC", -5: "PEPS_ETIMEOUT"}

@@ -45,15 +45,20 @@ bool shape_ok(const peps_shape* s, std::string* why) {
   if (s->L < 2 || s->L > PEPS_MAXL) { *why = "L must be in [2, 32]"; return false; }
   if (s->D < 1 || s->D > 8) { *why = "D must be in [1, 8]"; return false; }
   if (s->Dc < 1 || s->Dc * s->D > 256) { *why = "Dc must be >= 1 with Dc*D <= 256"; return false; }
-  if (s->precision != PEPS_FP64 && s->precision != PEPS_MIXED) { *why = "precision must be PEPS_FP64 or PEPS_MIXED"; return false; }
+  if (s->precision != PEPS_FP64 && s->precision != PEPS_MIXED && s->precision != PEPS_FP32) {
+    *why = "precision must be PEPS_FP64, PEPS_MIXED or PEPS_FP32";
+    return false;
+  }
   if (!std::isfinite(s->J1) || !std::isfinite(s->J2)) { *why = "J1, J2 must be finite"; return false; }
   return true;
 }
 
 cudaError_t launch_eval_form(const EvalArgs<double>& a, int g, cudaStream_t s) { return peps_launch_eval_f64(a, g, s); }
 cudaError_t launch_eval_form(const EvalArgs<ff>& a, int g, cudaStream_t s) { return peps_launch_eval_ff(a, g, s); }
+cudaError_t launch_eval_form(const EvalArgs<float>& a, int g, cudaStream_t s) { return peps_launch_eval_f32(a, g, s); }
 cudaError_t launch_sample_form(const SampleArgs<double>& a, int g, cudaStream_t s) { return peps_launch_sample_f64(a, g, s); }
 cudaError_t launch_sample_form(const SampleArgs<ff>& a, int g, cudaStream_t s) { return peps_launch_sample_ff(a, g, s); }
+cudaError_t launch_sample_form(const SampleArgs<float>& a, int g, cudaStream_t s) { return peps_launch_sample_f32(a, g, s); }
 
 int64_t up32(int64_t x) { return (x + 31) & ~int64_t(31); }
 
@@ -127,7 +132,9 @@ void make_plan(const peps_shape& s, int nslots, PepsPlan* P, std::vector<PepsSte
 
 int64_t psum_len(const PepsPlan& P) { return 2 * (int64_t)P.N * 2 * P.D4 + 1; }
 
-size_t elem_size(int precision) { return precision == PEPS_FP64 ? sizeof(double) : sizeof(ff); }
+size_t elem_size(int precision) {
+  return precision == PEPS_FP64 ? sizeof(double) : precision == PEPS_FP32 ? sizeof(float) : sizeof(ff);
+}
 
 int default_slots() {
   int dev = 0, sms = 0;
@@ -198,6 +205,9 @@ int eval_common(peps_ctx* c, const uint8_t* spins, int64_t B, int energy, int de
   if (c->shape.precision == PEPS_FP64)
     return launch_eval<double>(c, spins, B, energy, delta_on, e_in, e_loc, log_abs, sign, ratios,
                                n_flips, delta, sd, sde, se, accumulate, st);
+  if (c->shape.precision == PEPS_FP32)
+    return launch_eval<float>(c, spins, B, energy, delta_on, e_in, e_loc, log_abs, sign, ratios,
+                              n_flips, delta, sd, sde, se, accumulate, st);
   return launch_eval<ff>(c, spins, B, energy, delta_on, e_in, e_loc, log_abs, sign, ratios,
                          n_flips, delta, sd, sde, se, accumulate, st);
 }
@@ -382,6 +392,9 @@ int peps_sample_batch(peps_ctx* c, uint64_t seed, int64_t n_chains, int64_t chai
   if (c->shape.precision == PEPS_FP64)
     return launch_sample<double>(c, seed, n_chains, chain_offset, n_burn, n_thin, samples_per_chain,
                                  first_sweep, spins_out, chain_state, accepted, st);
+  if (c->shape.precision == PEPS_FP32)
+    return launch_sample<float>(c, seed, n_chains, chain_offset, n_burn, n_thin, samples_per_chain,
+                                first_sweep, spins_out, chain_state, accepted, st);
   return launch_sample<ff>(c, seed, n_chains, chain_offset, n_burn, n_thin, samples_per_chain,
                            first_sweep, spins_out, chain_state, accepted, st);
 }

@@ -2,6 +2,7 @@
 // Philox4x32-10 generator.
 //
 //   double : the FP64 form.
+//   float  : the FP32 form (FP32 tensors, factorisations and contractions).
 //   ff     : a float-float value hi + lo (two FP32, |lo| <= ulp(hi)/2), about
 //            48 significand bits, computed on the FP32 pipes.  The
 //            error-free transformations are the classical ones: TwoSum
@@ -91,6 +92,21 @@ template <> struct Arith<double> {
   PEPS_HD static double eps() { return 1.1102230246251565e-16; }
 };
 
+template <> struct Arith<float> {
+  typedef float acc_t;
+  PEPS_HD static float zero() { return 0.0f; }
+  PEPS_HD static float one() { return 1.0f; }
+  PEPS_HD static float from(double x) { return (float)x; }
+  PEPS_HD static double to(float x) { return (double)x; }
+  PEPS_HD static float hi(float x) { return x; }
+  PEPS_HD static void acc_init(acc_t& a) { a = 0.0f; }
+  PEPS_HD static void mac(acc_t& a, float x, float y) { a = fmaf(x, y, a); }
+  PEPS_HD static float acc_get(const acc_t& a) { return a; }
+  PEPS_HD static float sqrt_(float x) { return sqrtf(x); }
+  PEPS_HD static float scale(float x, double s) { return x * (float)s; }
+  PEPS_HD static double eps() { return 5.9604644775390625e-08; }  // 2^-24
+};
+
 // Compensated dot-product accumulator: the products' high parts are summed
 // with TwoSum, every rounding error and low-order product term goes to c.
 struct ffacc {
@@ -119,6 +135,13 @@ template <> struct Arith<ff> {
   PEPS_HD static ff scale(ff x, double s) { return x * ff_from_double(s); }
   PEPS_HD static double eps() { return 3.552713678800501e-15; }  // 2^-48
 };
+
+// Butterfly shuffle of a scalar of the form (components moved separately).
+PEPS_HD double shfl_xor_r(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+PEPS_HD float shfl_xor_r(float v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+PEPS_HD ff shfl_xor_r(ff v, int o) {
+  return ff{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+}
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), from its definition:

@@ -11,34 +11,55 @@
 #include "peps_plan.h"
 
 #define PEPS_NT 256          // threads per block
+#ifndef PEPS_WARP
+#define PEPS_WARP 32         // lanes per warp
+#endif
 #define PEPS_JACOBI_MAXSWEEP 40
 
 // ---------------------------------------------------------------------------
-// Block-wide reductions through shared memory.
+// Warp- and block-wide reductions (warp shuffles, one shared slot per warp).
 // ---------------------------------------------------------------------------
+template <class R>
+__device__ __forceinline__ R warp_sum(R v) {
+  for (int o = PEPS_WARP / 2; o > 0; o >>= 1) v = v + shfl_xor_r(v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+  for (int o = PEPS_WARP / 2; o > 0; o >>= 1) v = fmax(v, shfl_xor_r(v, o));
+  return v;
+}
+
 __device__ __forceinline__ double block_max(double v, double* red) {
-  const int t = threadIdx.x, nt = blockDim.x;
-  red[t] = v;
+  const int t = threadIdx.x, lane = t % PEPS_WARP, wid = t / PEPS_WARP,
+            nw = (blockDim.x + PEPS_WARP - 1) / PEPS_WARP;
+  v = warp_max(v);
+  if (lane == 0) red[wid] = v;
   __syncthreads();
-  for (int s = nt >> 1; s > 0; s >>= 1) {
-    if (t < s) red[t] = fmax(red[t], red[t + s]);
-    __syncthreads();
+  if (wid == 0) {
+    double x = lane < nw ? red[lane] : 0.0;
+    x = warp_max(x);
+    if (lane == 0) red[PEPS_NT / PEPS_WARP] = x;
   }
-  double r = red[0];
+  __syncthreads();
+  double r = red[PEPS_NT / PEPS_WARP];
   __syncthreads();
   return r;
 }
 
 template <class R>
 __device__ __forceinline__ R block_sum(R v, R* red) {
-  const int t = threadIdx.x, nt = blockDim.x;
-  red[t] = v;
+  const int t = threadIdx.x, lane = t % PEPS_WARP, wid = t / PEPS_WARP,
+            nw = (blockDim.x + PEPS_WARP - 1) / PEPS_WARP;
+  v = warp_sum<R>(v);
+  if (lane == 0) red[wid] = v;
   __syncthreads();
-  for (int s = nt >> 1; s > 0; s >>= 1) {
-    if (t < s) red[t] = red[t] + red[t + s];
-    __syncthreads();
+  if (wid == 0) {
+    R x = lane < nw ? red[lane] : Arith<R>::zero();
+    x = warp_sum<R>(x);
+    if (lane == 0) red[PEPS_NT / PEPS_WARP] = x;
   }
-  R r = red[0];
+  __syncthreads();
+  R r = red[PEPS_NT / PEPS_WARP];
   __syncthreads();
   return r;
 }
@@ -108,65 +129,60 @@ __device__ double normalize_pow2(R* x, int n, double* red) {
 
 // ---------------------------------------------------------------------------
 // Householder QR, R factor only (LAPACK-style reflectors H = I - tau v v^T,
-// v_k = 1).  X is m x n row-major (ld n), overwritten; R = the first
-// min(m,n) rows of the upper triangle are written to Rout (ld n), zeros
-// below the diagonal.  wbuf: n scalars of scratch (shared or global).
+// v_k = 1).  X is m x n COLUMN-major (X[c*m + i]), overwritten.  The first
+// min(m,n) rows of R are written row-major to Rout (ld n), zeros below the
+// diagonal.  Warp 0 forms each reflector; then one warp per column applies
+// it (dot product and update over contiguous rows).
 // ---------------------------------------------------------------------------
 template <class R>
-__device__ void householder_r(R* X, int m, int n, R* Rout, R* wbuf, R* redR,
-                              double* sh) {
+__device__ void householder_r(R* X, int m, int n, R* Rout, R* sh) {
   typedef Arith<R> M;
-  const int t = threadIdx.x, nt = blockDim.x;
+  const int t = threadIdx.x, lane = t % PEPS_WARP, wid = t / PEPS_WARP,
+            nw = (blockDim.x + PEPS_WARP - 1) / PEPS_WARP;
   const int kmax = m < n ? m : n;
   for (int k = 0; k < kmax; ++k) {
-    // squared norm of the column below the diagonal
-    typename M::acc_t a;
-    M::acc_init(a);
-    for (int i = k + 1 + t; i < m; i += nt) M::mac(a, X[i * n + k], X[i * n + k]);
-    R xn2 = block_sum<R>(M::acc_get(a), redR);
-    if (t == 0) {
-      R alpha = X[k * n + k];
-      double x2 = M::to(xn2);
-      if (!(x2 > 0.0)) {
-        sh[0] = 0.0;  // tau = 0: H = I
-      } else {
-        R nrm = M::sqrt_(alpha * alpha + xn2);
-        R beta = M::to(alpha) >= 0.0 ? -nrm : nrm;
-        R tau = (beta - alpha) / beta;
-        R scl = M::one() / (alpha - beta);
-        X[k * n + k] = beta;
-        sh[0] = 1.0;
-        redR[0] = tau;
-        redR[1] = scl;
+    R* xk = X + (int64_t)k * m;
+    if (wid == 0) {
+      typename M::acc_t a;
+      M::acc_init(a);
+      for (int i = k + 1 + lane; i < m; i += PEPS_WARP) M::mac(a, xk[i], xk[i]);
+      R xn2 = warp_sum<R>(M::acc_get(a));
+      if (lane == 0) {
+        R alpha = xk[k];
+        if (!(M::to(xn2) > 0.0)) {
+          sh[0] = M::zero();  // tau = 0: H = I
+        } else {
+          R nrm = M::sqrt_(alpha * alpha + xn2);
+          R beta = M::to(alpha) >= 0.0 ? -nrm : nrm;
+          sh[0] = (beta - alpha) / beta;
+          sh[1] = M::one() / (alpha - beta);
+          xk[k] = beta;
+        }
       }
+      __syncwarp();
+      R tau = sh[0], scl = sh[1];
+      if (M::to(tau) != 0.0)
+        for (int i = k + 1 + lane; i < m; i += PEPS_WARP) xk[i] = xk[i] * scl;
     }
     __syncthreads();
-    if (sh[0] != 0.0) {
-      R tau = redR[0], scl = redR[1];
-      for (int i = k + 1 + t; i < m; i += nt) X[i * n + k] = X[i * n + k] * scl;
-      __syncthreads();
-      // w_c = tau * (X[k][c] + sum_{i>k} v_i X[i][c]),  c > k
-      for (int c = k + 1 + t; c < n; c += nt) {
-        typename M::acc_t s;
-        M::acc_init(s);
-        M::mac(s, M::one(), X[k * n + c]);
-        for (int i = k + 1; i < m; ++i) M::mac(s, X[i * n + k], X[i * n + c]);
-        wbuf[c] = tau * M::acc_get(s);
-      }
-      __syncthreads();
-      const int w = n - k - 1;
-      const int tot = (m - k) * w;
-      for (int o = t; o < tot; o += nt) {
-        int i = k + o / w, c = k + 1 + o % w;
-        R v = (i == k) ? M::one() : X[i * n + k];
-        X[i * n + c] = X[i * n + c] - v * wbuf[c];
+    const R tau = sh[0];
+    if (M::to(tau) != 0.0) {
+      for (int c = k + 1 + wid; c < n; c += nw) {
+        R* xc = X + (int64_t)c * m;
+        typename M::acc_t a;
+        M::acc_init(a);
+        if (lane == 0) M::mac(a, M::one(), xc[k]);
+        for (int i = k + 1 + lane; i < m; i += PEPS_WARP) M::mac(a, xk[i], xc[i]);
+        R wv = tau * warp_sum<R>(M::acc_get(a));
+        if (lane == 0) xc[k] = xc[k] - wv;
+        for (int i = k + 1 + lane; i < m; i += PEPS_WARP) xc[i] = xc[i] - xk[i] * wv;
       }
     }
     __syncthreads();
   }
-  for (int o = t; o < kmax * n; o += nt) {
+  for (int o = t; o < kmax * n; o += blockDim.x) {
     int i = o / n, c = o % n;
-    Rout[o] = (c >= i) ? X[i * n + c] : M::zero();
+    Rout[o] = (c >= i) ? X[(int64_t)c * m + i] : M::zero();
   }
   __syncthreads();
 }
@@ -177,119 +193,97 @@ __device__ void householder_r(R* X, int m, int n, R* Rout, R* wbuf, R* redR,
 // are then sigma_i v_i^T with v_i the right singular vectors of X.  Writes
 // the kk rows of largest norm, normalised, to VT (kk x n) in decreasing
 // order (zero rows for zero singular values).  Pairs are visited in the
-// round-robin (circle) order, rr/2 disjoint pairs at a time.  Rows whose
-// squared norm is below eps^2 times the largest are left alone (their
-// singular values are below rounding level and they take no part in the
-// kept subspace beyond it).
+// round-robin (circle) order: the rr/2 disjoint pairs of a round are taken
+// one per warp (dot product, rotation and update inside the warp), with one
+// barrier per round.  Rows whose squared norm is below eps^2 times the
+// largest are left alone (their singular values are below rounding level).
 // alpha: rr doubles of scratch.  Returns the number of sweeps used.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ int rr_player(int pos, int rd, int rp) {
+  return pos == 0 ? 0 : ((pos - 1 + rd) % (rp - 1)) + 1;
+}
+
+template <class R>
+__device__ void row_norms(const R* X, int rr, int n, double* alpha) {
+  typedef Arith<R> M;
+  const int lane = threadIdx.x % PEPS_WARP, wid = threadIdx.x / PEPS_WARP,
+            nw = (blockDim.x + PEPS_WARP - 1) / PEPS_WARP;
+  for (int p = wid; p < rr; p += nw) {
+    typename M::acc_t a;
+    M::acc_init(a);
+    for (int e = lane; e < n; e += PEPS_WARP) M::mac(a, X[p * n + e], X[p * n + e]);
+    R s = warp_sum<R>(M::acc_get(a));
+    if (lane == 0) alpha[p] = M::to(s);
+  }
+  __syncthreads();
+}
+
 template <class R>
 __device__ int jacobi_rows(R* X, int rr, int n, int kk, R* VT, double* alpha,
-                           R* part, double* rot, int* shi, double* red,
-                           int* flags) {
+                           int* shi, double* red, int* flags) {
   typedef Arith<R> M;
-  const int t = threadIdx.x, nt = blockDim.x;
+  const int t = threadIdx.x, lane = t % PEPS_WARP, wid = t / PEPS_WARP,
+            nw = (blockDim.x + PEPS_WARP - 1) / PEPS_WARP;
   const int rp = rr + (rr & 1);
   const int npair = rp / 2;
   const double tol = (double)n * M::eps();
-  // exact squared row norms
-  for (int p = 0; p < rr; ++p) {
-    typename M::acc_t a;
-    M::acc_init(a);
-    for (int e = t; e < n; e += nt) M::mac(a, X[p * n + e], X[p * n + e]);
-    R s = block_sum<R>(M::acc_get(a), part);
-    if (t == 0) alpha[p] = M::to(s);
-  }
-  __syncthreads();
+  row_norms<R>(X, rr, n, alpha);
   int sweep = 0;
   for (; sweep < PEPS_JACOBI_MAXSWEEP && rr > 1; ++sweep) {
     double amax = 0.0;
-    for (int p = t; p < rr; p += nt) amax = fmax(amax, alpha[p]);
+    for (int p = t; p < rr; p += blockDim.x) amax = fmax(amax, alpha[p]);
     const double thr = block_max(amax, red) * M::eps() * M::eps();
     if (t == 0) shi[0] = 0;
     __syncthreads();
     for (int rd = 0; rd < rp - 1; ++rd) {
-      // team of tm threads per pair computes gamma = x_p . x_q
-      int tm = nt / npair;
-      if (tm < 1) tm = 1;
-      for (int base = 0; base < npair; base += nt / tm) {
-        int pr = base + t / tm, mb = t % tm;
+      for (int pr = wid; pr < npair; pr += nw) {
+        const int pp = rr_player(pr, rd, rp), qq = rr_player(rp - 1 - pr, rd, rp);
+        if (pp >= rr || qq >= rr) continue;
+        R* xp = X + pp * n;
+        R* xq = X + qq * n;
         typename M::acc_t a;
         M::acc_init(a);
-        if (pr < npair && t / tm < nt / tm) {
-          int pp = (pr == 0) ? 0 : ((pr - 1 + rd) % (rp - 1)) + 1;
-          int qpos = rp - 1 - pr;
-          int qq = (qpos == 0) ? 0 : ((qpos - 1 + rd) % (rp - 1)) + 1;
-          if (pp < rr && qq < rr)
-            for (int e = mb; e < n; e += tm) M::mac(a, X[pp * n + e], X[qq * n + e]);
-        }
-        if (t / tm < nt / tm) part[t] = M::acc_get(a);
-        __syncthreads();
-        if (t < nt / tm && base + t < npair) {
-          R g = M::zero();
-          for (int u = 0; u < tm; ++u) g = g + part[t * tm + u];
-          int pr2 = base + t;
-          int pp = (pr2 == 0) ? 0 : ((pr2 - 1 + rd) % (rp - 1)) + 1;
-          int qpos = rp - 1 - pr2;
-          int qq = (qpos == 0) ? 0 : ((qpos - 1 + rd) % (rp - 1)) + 1;
-          double c = 1.0, s = 0.0;
-          if (pp < rr && qq < rr) {
-            double gam = M::to(g), ap = alpha[pp], aq = alpha[qq];
-            if (ap > thr && aq > thr && fabs(gam) > tol * sqrt(ap * aq)) {
-              double zeta = (aq - ap) / (2.0 * gam);
-              double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-              c = 1.0 / sqrt(1.0 + tt * tt);
-              s = c * tt;
-              alpha[pp] = ap - tt * gam;
-              alpha[qq] = aq + tt * gam;
-              shi[0] = 1;
-            }
+        for (int e = lane; e < n; e += PEPS_WARP) M::mac(a, xp[e], xq[e]);
+        const double gam = M::to(warp_sum<R>(M::acc_get(a)));
+        double c = 1.0, s = 0.0;
+        const double ap = alpha[pp], aq = alpha[qq];
+        if (ap > thr && aq > thr && fabs(gam) > tol * sqrt(ap * aq)) {
+          double zeta = (aq - ap) / (2.0 * gam);
+          double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          c = 1.0 / sqrt(1.0 + tt * tt);
+          s = c * tt;
+          __syncwarp();
+          if (lane == 0) {
+            alpha[pp] = ap - tt * gam;
+            alpha[qq] = aq + tt * gam;
+            shi[0] = 1;
           }
-          rot[2 * pr2] = c;
-          rot[2 * pr2 + 1] = s;
+          const R cr = M::from(c), sr = M::from(s);
+          for (int e = lane; e < n; e += PEPS_WARP) {
+            R u = xp[e], v = xq[e];
+            xp[e] = cr * u - sr * v;
+            xq[e] = sr * u + cr * v;
+          }
         }
-        __syncthreads();
-      }
-      // apply the rotations: x_p <- c x_p - s x_q, x_q <- s x_p + c x_q
-      const int tot = npair * n;
-      for (int o = t; o < tot; o += nt) {
-        int pr = o / n, e = o % n;
-        double s = rot[2 * pr + 1];
-        if (s == 0.0) continue;
-        int pp = (pr == 0) ? 0 : ((pr - 1 + rd) % (rp - 1)) + 1;
-        int qpos = rp - 1 - pr;
-        int qq = (qpos == 0) ? 0 : ((qpos - 1 + rd) % (rp - 1)) + 1;
-        R c = M::from(rot[2 * pr]), sr = M::from(s);
-        R xp = X[pp * n + e], xq = X[qq * n + e];
-        X[pp * n + e] = c * xp - sr * xq;
-        X[qq * n + e] = sr * xp + c * xq;
       }
       __syncthreads();
     }
-    int any = shi[0];
-    // refresh the norms exactly
-    for (int p = 0; p < rr; ++p) {
-      typename M::acc_t a;
-      M::acc_init(a);
-      for (int e = t; e < n; e += nt) M::mac(a, X[p * n + e], X[p * n + e]);
-      R s = block_sum<R>(M::acc_get(a), part);
-      if (t == 0) alpha[p] = M::to(s);
-    }
-    __syncthreads();
+    const int any = shi[0];
+    row_norms<R>(X, rr, n, alpha);
     if (!any) break;
   }
   if (sweep >= PEPS_JACOBI_MAXSWEEP && t == 0) atomicOr(flags, 4);
   // rank rows by norm (ties by index) and write the kk largest, normalised
-  for (int p = t; p < rr; p += nt) {
+  for (int p = t; p < rr; p += blockDim.x) {
     int rank = 0;
     for (int q = 0; q < rr; ++q)
       rank += (alpha[q] > alpha[p]) || (alpha[q] == alpha[p] && q < p);
     shi[1 + p] = rank;
   }
   __syncthreads();
-  for (int o = t; o < kk * n; o += nt) VT[o] = M::zero();
+  for (int o = t; o < kk * n; o += blockDim.x) VT[o] = M::zero();
   __syncthreads();
-  for (int o = t; o < rr * n; o += nt) {
+  for (int o = t; o < rr * n; o += blockDim.x) {
     int p = o / n, e = o % n;
     int rank = shi[1 + p];
     if (rank < kk && alpha[p] > 0.0)

@@ -28,6 +28,8 @@ cudaError_t peps_launch_convert(int precision, const double* A, void* As, int64_
   int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
   if (precision == PEPS_FP64)
     peps_convert_kernel<double><<<grid, 256, 0, st>>>(A, static_cast<double*>(As), n, flags);
+  else if (precision == PEPS_FP32)
+    peps_convert_kernel<float><<<grid, 256, 0, st>>>(A, static_cast<float*>(As), n, flags);
   else
     peps_convert_kernel<ff><<<grid, 256, 0, st>>>(A, static_cast<ff*>(As), n, flags);
   return cudaGetLastError();
@@ -40,6 +42,9 @@ cudaError_t peps_launch_grad(int precision, const double* sd, const double* sde,
   if (precision == PEPS_FP64)
     peps_grad_kernel<double><<<grid, 256, 0, st>>>(sd, sde, se, M, dt, k0, k1, step, A,
                                                    static_cast<double*>(As), n);
+  else if (precision == PEPS_FP32)
+    peps_grad_kernel<float><<<grid, 256, 0, st>>>(sd, sde, se, M, dt, k0, k1, step, A,
+                                                  static_cast<float*>(As), n);
   else
     peps_grad_kernel<ff><<<grid, 256, 0, st>>>(sd, sde, se, M, dt, k0, k1, step, A,
                                                static_cast<ff*>(As), n);

@@ -10,8 +10,10 @@ template <class R> struct SampleArgs;
 
 cudaError_t peps_launch_eval_f64(const EvalArgs<double>& a, int grid, cudaStream_t st);
 cudaError_t peps_launch_eval_ff(const EvalArgs<ff>& a, int grid, cudaStream_t st);
+cudaError_t peps_launch_eval_f32(const EvalArgs<float>& a, int grid, cudaStream_t st);
 cudaError_t peps_launch_sample_f64(const SampleArgs<double>& a, int grid, cudaStream_t st);
 cudaError_t peps_launch_sample_ff(const SampleArgs<ff>& a, int grid, cudaStream_t st);
+cudaError_t peps_launch_sample_f32(const SampleArgs<float>& a, int grid, cudaStream_t st);
 cudaError_t peps_launch_reduce(const double* psum, int nslots, int64_t len, double* sd,
                                double* sde, double* se, int accumulate, cudaStream_t st);
 cudaError_t peps_launch_convert(int precision, const double* A, void* As, int64_t n, int* flags,

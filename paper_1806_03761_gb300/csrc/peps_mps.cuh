@@ -107,16 +107,18 @@ __device__ double compress_row(const PepsPlan& P, const PepsStep& st, bool above
     c.sc[0] = Dl * p * b; c.sc[1] = p * b; c.sc[2] = b; c.sc[3] = 1;
     c.k1 = a; c.ka1 = Dl; c.kb1 = p * b;
     contract<R>(c, Rp, Mj, w.b0);
-    // X[(x,q)][(b',r)] = sum_{l,p'} S1[x][l][p'][b'] T[l][r][p'][q]
+    // X[(x,q)][(b',r)] = sum_{l,p'} S1[x][l][p'][b'] T[l][r][p'][q], stored
+    // column-major (column (b',r), row (x,q)) for the Householder sweep
+    const int mrow = rprev * Q;
     c = ctr_init();
     c.e[0] = rprev; c.e[1] = Q; c.e[2] = b; c.e[3] = Dr;
     c.sa[0] = Dl * p * b; c.sa[2] = 1;
     c.sb[1] = sQ; c.sb[3] = D2;
-    c.sc[0] = Q * Bj; c.sc[1] = Bj; c.sc[2] = Dr; c.sc[3] = 1;
+    c.sc[0] = Q; c.sc[1] = 1; c.sc[2] = Dr * mrow; c.sc[3] = mrow;
     c.k1 = Dl; c.ka1 = p * b; c.kb1 = D3;
     c.k2 = p; c.ka2 = b; c.kb2 = sP;
     contract<R>(c, w.b0, T, w.b1);
-    householder_r<R>(w.b1, rprev * Q, Bj, w.rst + (int64_t)(j + 1) * MC, w.wsh, w.redR, w.red);
+    householder_r<R>(w.b1, mrow, Bj, w.rst + (int64_t)(j + 1) * MC, w.wsh);
     rprev = st.r[j];
     // only the row space of R_j matters: keep it at unit scale so that the
     // float-float form stays inside the FP32 exponent range
@@ -162,21 +164,22 @@ __device__ double compress_row(const PepsPlan& P, const PepsStep& st, bool above
       logs += normalize_pow2<R>(out, n, w.red);
       break;
     }
-    // X_j = R_{j-1} Y_j : rr x n
+    // X_j = R_{j-1} Y_j : rr x n (column-major when a QR reduces it first)
     const int rr = (j >= 1) ? st.r[j - 1] : 1;
     c = ctr_init();
     c.e[0] = rr; c.e[1] = n;
-    c.sa[0] = Aj; c.sb[1] = 1; c.sc[0] = n; c.sc[1] = 1;
+    c.sa[0] = Aj; c.sb[1] = 1;
+    if (rr > n) { c.sc[0] = 1; c.sc[1] = rr; } else { c.sc[0] = n; c.sc[1] = 1; }
     c.k1 = Aj; c.ka1 = 1; c.kb1 = n;
     contract<R>(c, w.rst + (int64_t)j * MC, Y, w.xj);
     const int kk = st.oa[j];
     R* V = Mout + (int64_t)j * SC;  // V^T (kk x n) is the truncated site j
     normalize_pow2<R>(w.xj, rr * n, w.red);
     if (rr > n) {
-      householder_r<R>(w.xj, rr, n, w.b2, w.wsh, w.redR, w.red);
-      jacobi_rows<R>(w.b2, n, n, kk, V, w.alpha, w.redR, w.rot, w.ish, w.red, w.flags);
+      householder_r<R>(w.xj, rr, n, w.b2, w.wsh);
+      jacobi_rows<R>(w.b2, n, n, kk, V, w.alpha, w.ish, w.red, w.flags);
     } else {
-      jacobi_rows<R>(w.xj, rr, n, kk, V, w.alpha, w.redR, w.rot, w.ish, w.red, w.flags);
+      jacobi_rows<R>(w.xj, rr, n, kk, V, w.alpha, w.ish, w.red, w.flags);
     }
     // C_j[(a,l)][k] = sum_{(q,c)} Y[(a,l)][(q,c)] V^T[k][(q,c)]
     c = ctr_init();

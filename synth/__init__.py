@@ -14,11 +14,13 @@ Workload recipes (stand-ins for the SU-initialised PEPS the paper reads from
 a file, which is not available):
   * "gauss":  A ~ N(0, 1) / D                      (i.i.d. entries)
   * "neel":   A = P_neel + eps * G, G ~ N(0, 1) / D^2, where P_neel is the
-              Neel product state: P(s, 0, 0, 0, 0) = [s == (i + j) mod 2].
+              Neel product state: P(s, 0, 0, 0, 0) = [s == (i + j) mod 2]
+              (eps = 1e-2 for the 8x8 workload).
 """
 import numpy as np
 
-__all__ = ["make_peps", "random_sz0_configs", "neel_config", "CONFIGS"]
+__all__ = ["make_peps", "random_sz0_configs", "neel_config", "near_neel_configs",
+           "CONFIGS", "workload"]
 
 
 def make_peps(L, D, seed, kind="gauss", eps=1e-2):
@@ -53,6 +55,29 @@ def random_sz0_configs(L, B, seed):
 def neel_config(L):
     """The Neel configuration s_m = (i + j) mod 2 as uint8[N]."""
     return np.array([(m // L + m % L) % 2 for m in range(L * L)], np.uint8)
+
+
+def near_neel_configs(L, B, seed, n_moves):
+    """B configurations obtained from the Neel configuration by n_moves
+    random exchanges of antiparallel nearest-neighbour pairs (numpy
+    PCG64(seed)); S^z = 0 is kept.  Typical configurations of a Neel-like
+    state's W^2 distribution lie this close to the Neel configuration."""
+    rng = np.random.default_rng(seed)
+    N = L * L
+    pairs = [(i * L + j, i * L + j + 1) for i in range(L) for j in range(L - 1)]
+    pairs += [(i * L + j, (i + 1) * L + j) for i in range(L - 1) for j in range(L)]
+    pairs = np.array(pairs)
+    out = np.empty((B, N), np.uint8)
+    for b in range(B):
+        s = neel_config(L).copy()
+        done = 0
+        while done < n_moves:
+            a, c = pairs[rng.integers(len(pairs))]
+            if s[a] != s[c]:
+                s[a], s[c] = s[c], s[a]
+                done += 1
+        out[b] = s
+    return out
 
 
 # The workloads: shapes, truncation, recipe, seeds and batch sizes.
