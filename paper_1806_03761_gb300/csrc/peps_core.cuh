@@ -83,9 +83,10 @@ __device__ __forceinline__ Ctr ctr_init() {
   return d;
 }
 
+// The operands are scratch rewritten within the same kernel, so they are
+// read through the coherent path (no __restrict__ / read-only cache).
 template <class R>
-__device__ void contract(const Ctr& d, const R* __restrict__ A,
-                         const R* __restrict__ B, R* __restrict__ C) {
+__device__ void contract(const Ctr& d, const R* A, const R* B, R* C) {
   typedef Arith<R> M;
   const int tot = d.e[0] * d.e[1] * d.e[2] * d.e[3] * d.e[4];
   for (int o = threadIdx.x; o < tot; o += blockDim.x) {
@@ -193,37 +194,50 @@ __device__ void householder_r(R* X, int m, int n, R* Rout, R* sh) {
 // are then sigma_i v_i^T with v_i the right singular vectors of X.  Writes
 // the kk rows of largest norm, normalised, to VT (kk x n) in decreasing
 // order (zero rows for zero singular values).  Pairs are visited in the
-// round-robin (circle) order: the rr/2 disjoint pairs of a round are taken
-// one per warp (dot product, rotation and update inside the warp), with one
-// barrier per round.  Rows whose squared norm is below eps^2 times the
+// round-robin (circle) order; the rr/2 disjoint pairs of a round are spread
+// over groups of PEPS_JG lanes (dot product, rotation and update inside the
+// group), with one barrier per round.  The rotation is computed in the
+// form's own arithmetic.  Rows whose squared norm is below eps^2 times the
 // largest are left alone (their singular values are below rounding level).
-// alpha: rr doubles of scratch.  Returns the number of sweeps used.
+// alpha: rr scalars of scratch.  Returns the number of sweeps used.
 // ---------------------------------------------------------------------------
+#ifndef PEPS_JG
+#define PEPS_JG (PEPS_WARP >= 8 ? 8 : PEPS_WARP)  // lanes per rotation pair
+#endif
+
 __device__ __forceinline__ int rr_player(int pos, int rd, int rp) {
   return pos == 0 ? 0 : ((pos - 1 + rd) % (rp - 1)) + 1;
 }
 
 template <class R>
-__device__ void row_norms(const R* X, int rr, int n, double* alpha) {
+__device__ __forceinline__ R group_sum(R v) {
+  for (int o = PEPS_JG / 2; o > 0; o >>= 1) v = v + shfl_xor_r(v, o);
+  return v;
+}
+
+template <class R>
+__device__ void row_norms(const R* X, int rr, int n, R* alpha) {
   typedef Arith<R> M;
-  const int lane = threadIdx.x % PEPS_WARP, wid = threadIdx.x / PEPS_WARP,
-            nw = (blockDim.x + PEPS_WARP - 1) / PEPS_WARP;
-  for (int p = wid; p < rr; p += nw) {
+  const int g = threadIdx.x / PEPS_JG, gl = threadIdx.x % PEPS_JG;
+  const int ng = blockDim.x / PEPS_JG;
+  for (int base = 0; base < rr; base += ng) {
+    const int p = base + g;
     typename M::acc_t a;
     M::acc_init(a);
-    for (int e = lane; e < n; e += PEPS_WARP) M::mac(a, X[p * n + e], X[p * n + e]);
-    R s = warp_sum<R>(M::acc_get(a));
-    if (lane == 0) alpha[p] = M::to(s);
+    if (p < rr)
+      for (int e = gl; e < n; e += PEPS_JG) M::mac(a, X[p * n + e], X[p * n + e]);
+    R s = group_sum<R>(M::acc_get(a));
+    if (p < rr && gl == 0) alpha[p] = s;
   }
   __syncthreads();
 }
 
 template <class R>
-__device__ int jacobi_rows(R* X, int rr, int n, int kk, R* VT, double* alpha,
+__device__ int jacobi_rows(R* X, int rr, int n, int kk, R* VT, R* alpha,
                            int* shi, double* red, int* flags) {
   typedef Arith<R> M;
-  const int t = threadIdx.x, lane = t % PEPS_WARP, wid = t / PEPS_WARP,
-            nw = (blockDim.x + PEPS_WARP - 1) / PEPS_WARP;
+  const int t = threadIdx.x;
+  const int g = t / PEPS_JG, gl = t % PEPS_JG, ng = blockDim.x / PEPS_JG;
   const int rp = rr + (rr & 1);
   const int npair = rp / 2;
   const double tol = (double)n * M::eps();
@@ -231,38 +245,47 @@ __device__ int jacobi_rows(R* X, int rr, int n, int kk, R* VT, double* alpha,
   int sweep = 0;
   for (; sweep < PEPS_JACOBI_MAXSWEEP && rr > 1; ++sweep) {
     double amax = 0.0;
-    for (int p = t; p < rr; p += blockDim.x) amax = fmax(amax, alpha[p]);
+    for (int p = t; p < rr; p += blockDim.x) amax = fmax(amax, (double)M::hi(alpha[p]));
     const double thr = block_max(amax, red) * M::eps() * M::eps();
     if (t == 0) shi[0] = 0;
     __syncthreads();
     for (int rd = 0; rd < rp - 1; ++rd) {
-      for (int pr = wid; pr < npair; pr += nw) {
-        const int pp = rr_player(pr, rd, rp), qq = rr_player(rp - 1 - pr, rd, rp);
-        if (pp >= rr || qq >= rr) continue;
-        R* xp = X + pp * n;
-        R* xq = X + qq * n;
+      for (int base = 0; base < npair; base += ng) {
+        const int pr = base + g;
+        int pp = rr, qq = rr;
+        if (pr < npair) { pp = rr_player(pr, rd, rp); qq = rr_player(rp - 1 - pr, rd, rp); }
+        const bool live = pp < rr && qq < rr;
+        R* xp = X + (live ? pp : 0) * n;
+        R* xq = X + (live ? qq : 0) * n;
         typename M::acc_t a;
         M::acc_init(a);
-        for (int e = lane; e < n; e += PEPS_WARP) M::mac(a, xp[e], xq[e]);
-        const double gam = M::to(warp_sum<R>(M::acc_get(a)));
-        double c = 1.0, s = 0.0;
-        const double ap = alpha[pp], aq = alpha[qq];
-        if (ap > thr && aq > thr && fabs(gam) > tol * sqrt(ap * aq)) {
-          double zeta = (aq - ap) / (2.0 * gam);
-          double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          c = 1.0 / sqrt(1.0 + tt * tt);
-          s = c * tt;
-          __syncwarp();
-          if (lane == 0) {
+        if (live)
+          for (int e = gl; e < n; e += PEPS_JG) M::mac(a, xp[e], xq[e]);
+        const R gam = group_sum<R>(M::acc_get(a));  // every lane of the group
+        if (!live) continue;
+        const R ap = alpha[pp], aq = alpha[qq];
+        const double gh = (double)M::hi(gam), aph = (double)M::hi(ap), aqh = (double)M::hi(aq);
+        if (aph > thr && aqh > thr && gh * gh > tol * tol * aph * aqh) {
+          // zeta = (a_q - a_p) / (2 gamma); t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2))
+          const R zeta = (aq - ap) / (gam + gam);
+          const R az = M::hi(zeta) >= 0 ? zeta : -zeta;
+          // for |zeta| > 2^50, sqrt(1 + zeta^2) = |zeta| to working precision
+          // (and zeta^2 could leave the FP32 exponent range)
+          R tt = (double)M::hi(az) > 1.125899906842624e15
+                     ? M::one() / (az + az)
+                     : M::one() / (az + M::sqrt_(M::one() + zeta * zeta));
+          if (M::hi(zeta) < 0) tt = -tt;
+          const R c = M::one() / M::sqrt_(M::one() + tt * tt);
+          const R s = c * tt;
+          for (int e = gl; e < n; e += PEPS_JG) {
+            R u = xp[e], v = xq[e];
+            xp[e] = c * u - s * v;
+            xq[e] = s * u + c * v;
+          }
+          if (gl == 0) {
             alpha[pp] = ap - tt * gam;
             alpha[qq] = aq + tt * gam;
             shi[0] = 1;
-          }
-          const R cr = M::from(c), sr = M::from(s);
-          for (int e = lane; e < n; e += PEPS_WARP) {
-            R u = xp[e], v = xq[e];
-            xp[e] = cr * u - sr * v;
-            xq[e] = sr * u + cr * v;
           }
         }
       }
@@ -273,11 +296,20 @@ __device__ int jacobi_rows(R* X, int rr, int n, int kk, R* VT, double* alpha,
     if (!any) break;
   }
   if (sweep >= PEPS_JACOBI_MAXSWEEP && t == 0) atomicOr(flags, 4);
+  // Rows at or below the threshold were never orthogonalised: they stand
+  // for singular values below eps * sigma_max and are written as zero rows,
+  // so that V^T V stays the projector onto an orthonormal kept subspace.
+  double amax = 0.0;
+  for (int p = t; p < rr; p += blockDim.x) amax = fmax(amax, (double)M::hi(alpha[p]));
+  const double thr = block_max(amax, red) * M::eps() * M::eps();
   // rank rows by norm (ties by index) and write the kk largest, normalised
   for (int p = t; p < rr; p += blockDim.x) {
     int rank = 0;
-    for (int q = 0; q < rr; ++q)
-      rank += (alpha[q] > alpha[p]) || (alpha[q] == alpha[p] && q < p);
+    const double ap = M::to(alpha[p]);
+    for (int q = 0; q < rr; ++q) {
+      const double aq = M::to(alpha[q]);
+      rank += (aq > ap) || (aq == ap && q < p);
+    }
     shi[1 + p] = rank;
   }
   __syncthreads();
@@ -286,8 +318,8 @@ __device__ int jacobi_rows(R* X, int rr, int n, int kk, R* VT, double* alpha,
   for (int o = t; o < rr * n; o += blockDim.x) {
     int p = o / n, e = o % n;
     int rank = shi[1 + p];
-    if (rank < kk && alpha[p] > 0.0)
-      VT[rank * n + e] = X[p * n + e] * M::from(1.0 / sqrt(alpha[p]));
+    if (rank < kk && (double)M::hi(alpha[p]) > thr)
+      VT[rank * n + e] = X[p * n + e] / M::sqrt_(alpha[p]);
   }
   __syncthreads();
   return sweep;

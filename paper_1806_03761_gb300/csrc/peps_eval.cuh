@@ -30,7 +30,7 @@ __device__ Work<R> make_work(const PepsPlan& P, R* ws, double* wsd, int slot) {
   w.r2 = base + P.off_r2;
   w.scl = bd + P.doff_scale;
   w.delta = bd + P.doff_delta;
-  w.alpha = bd + P.doff_alpha;
+  w.alpha = base + P.off_alpha;
   return w;
 }
 

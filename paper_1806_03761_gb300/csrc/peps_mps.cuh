@@ -32,7 +32,7 @@ struct Work {
   R* r2;
   double* scl;    // log-scales of the strip envs: 4 (L+1)
   double* delta;  // staged Delta of one sample: N D^4
-  double* alpha;  // Jacobi row norms
+  R* alpha;       // Jacobi row norms
   // shared memory
   double* red;
   R* redR;
