@@ -194,7 +194,8 @@ def main():
     ctx = P.PepsContext(L, D, Dc, precision=args.precision, slots=args.slots)
     ctx.set_tensors(A)
     seed = 0x5EED0000 + cfg["seed"]
-    chain_offset = rank * B
+    from paper_1806_03761_gb300.dist import allreduce_sums, shard
+    chain_offset, B = shard(rank, world, B)
     # chains start from their Fisher-Yates states; every step continues them
     state = ctx.sample(seed, B, 0, 1, 1, chain_offset=chain_offset, first_sweep=1)
     state = state.view(B, N).contiguous()
@@ -225,10 +226,7 @@ def main():
             e1.record(stream)
             ev_eval.append((e0, e1))
         # 3. GO update (sums all-reduced across ranks first)
-        if world > 1:
-            import torch.distributed as dist
-            for t in sums:
-                dist.all_reduce(t)
+        allreduce_sums(sums, world)
         ctx.grad_step(sums, B * world, args.dt, seed, step_no[0], A)
         step_no[0] += 1
 
