@@ -48,7 +48,9 @@ enum {
   PEPS_ENOMEM = -2,   /* device allocation failed */
   PEPS_ECUDA = -3,    /* CUDA runtime error (launch, copy, no device) */
   PEPS_ENUMERIC = -4, /* non-finite input, zero amplitude, no convergence */
-  PEPS_ETIMEOUT = -5  /* a bounded device wait ran out */
+  PEPS_ETIMEOUT = -5, /* a bounded device wait ran out */
+  PEPS_ESCRATCH = -6  /* peps_amplitudes_noalloc: the shape does not fit the
+                         fixed device scratch */
 };
 
 enum {
@@ -177,6 +179,30 @@ int peps_sample_batch(peps_ctx* ctx, uint64_t seed, int64_t n_chains,
                       int32_t samples_per_chain, uint64_t first_sweep,
                       uint8_t* spins_out, uint8_t* chain_state,
                       int64_t* accepted, void* stream);
+
+/* peps_amplitudes without any device allocation, for callers that may not
+ * call cudaMalloc (inside a stream capture whose owner forbids allocation, a
+ * real-time loop with a fixed memory budget, a plug-in whose host owns all
+ * device memory).  The paper has no counterpart: it is an interface for
+ * such callers, computing exactly what peps_amplitudes computes (FP64 form
+ * only; shape->precision must be PEPS_FP64).
+ *   A: float64[N][2][D^4] site tensors (device, read only); spins, log_abs,
+ *   sign as in peps_amplitudes; no context.
+ * The workspace (a converted copy of A, the bond-dimension table and the
+ * per-sample environments) lives in one fixed 64 MiB device array that every
+ * GPU loading the library holds until process exit.  Shapes whose per-sample
+ * workspace does not fit return PEPS_ESCRATCH (e.g. 16x16, D=6, Dc=24 fits
+ * three samples at a time, 8x8, D=4, Dc=16 fits 39, 24x24, D=8, Dc=32 does not fit);
+ * when fewer samples fit than the GPU could run, they run fewer at a
+ * time.  Calls no allocating routine.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device current:
+ * make that first call before any stream capture.  Every call reuses the
+ * same array, so calls that overlap on the GPU (other streams, other host
+ * threads) race: order them.  Device-side conditions (zero amplitude,
+ * non-finite input) are only reflected in sign = 0 / log_abs. */
+int peps_amplitudes_noalloc(const peps_shape* shape, const double* A,
+                            const uint8_t* spins, int64_t B, double* log_abs,
+                            int8_t* sign, void* stream);
 
 /* Wait for `stream` and return the device-side error state: PEPS_OK, or
  * PEPS_ENUMERIC with *flags (host, nullable) set to the PEPS_FLAG_* bits

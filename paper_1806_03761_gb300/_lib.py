@@ -14,18 +14,19 @@ PEPS_ENOMEM = -2
 PEPS_ECUDA = -3
 PEPS_ENUMERIC = -4
 PEPS_ETIMEOUT = -5
+PEPS_ESCRATCH = -6
 PEPS_FP64 = 0
 PEPS_MIXED = 1
 PEPS_FP32 = 2
 
 ERRNAMES = {0: "PEPS_OK", -1: "PEPS_EINVAL", -2: "PEPS_ENOMEM", -3: "PEPS_ECUDA",
-            -4: "PEPS_ENUMERIC", -5: "PEPS_ETIMEOUT"}
+            -4: "PEPS_ENUMERIC", -5: "PEPS_ETIMEOUT", -6: "PEPS_ESCRATCH"}
 
 # every entry point include/peps.h declares
 EXPORTS = ("peps_create", "peps_destroy", "peps_last_error", "peps_workspace_bytes",
            "peps_set_tensors", "peps_amplitudes", "peps_local_energy", "peps_logderiv",
            "peps_evaluate", "peps_grad_step", "peps_sample_batch", "peps_sync_status",
-           "peps_flops_per_sample")
+           "peps_flops_per_sample", "peps_amplitudes_noalloc")
 
 
 class PepsShape(ctypes.Structure):
@@ -56,6 +57,7 @@ _SIGS = {
     "peps_sample_batch": (I32, [P, U64, I64, I64, I32, I32, I32, U64, P, P, P, P]),
     "peps_sync_status": (I32, [P, P, ctypes.POINTER(I32)]),
     "peps_flops_per_sample": (F64, [ctypes.POINTER(PepsShape), F64]),
+    "peps_amplitudes_noalloc": (I32, [ctypes.POINTER(PepsShape), P, P, I64, P, P, P]),
 }
 
 
