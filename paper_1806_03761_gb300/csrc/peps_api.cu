@@ -119,7 +119,8 @@ void make_plan(const peps_shape& s, int nslots, PepsPlan* P, std::vector<PepsSte
   P->off_r1 = take((int64_t)(L + 1) * P->site_cap);
   P->off_l2 = take((int64_t)(L + 1) * P->env2_cap);
   P->off_r2 = take((int64_t)(L + 1) * P->env2_cap);
-  P->off_alpha = take((int64_t)Dc * D + 8);
+  P->off_alpha = take(3 * (int64_t)Dc * D + 16);
+  P->off_inv = take(13 * (int64_t)Dc * Dc * D);
   P->off_tmp = take(32);
   P->slot_elems = o;
   int64_t d = 0;

@@ -324,3 +324,321 @@ __device__ int jacobi_rows(R* X, int rr, int n, int kk, R* VT, R* alpha,
   __syncthreads();
   return sweep;
 }
+
+// ---------------------------------------------------------------------------
+// Top-kk right singular vectors of X (rr x n row-major, 1 <= rr <= n) by
+// Golub-Kahan bidiagonalisation, bisection and inverse iteration:
+//   1. A = X^T (n x rr, column c = row c of X) = Q B P^T with B upper
+//      bidiagonal (diagonal d, superdiagonal e); Householder reflectors from
+//      the left (kept: they form Q) and from the right (applied and dropped).
+//   2. The kk largest singular values of B by bisection on the count of
+//      singular values below x, from the stationary qd transform of
+//      B^T B - x^2 (relative accuracy in FP32; Demmel-Kahan).
+//   3. For each, inverse iteration in the form's arithmetic on the
+//      Golub-Kahan tridiagonal (zero diagonal, off-diagonals d0,e0,d1,...),
+//      whose eigenvector for +sigma interleaves (v_0, u_0, v_1, u_1, ...) with
+//      B v = sigma u; three solves with a partially pivoted LU.
+//   4. Gram-Schmidt on the u's (largest first), then V_i = Q [u_i; 0]: the
+//      right singular vectors of X.  Directions whose singular value is at or
+//      below eps * sigma_max are written as zero rows (as in jacobi_rows).
+// VT (kk x n) receives the vectors in decreasing order of sigma.
+// aux: >= 3 rr + 8 scalars; inv: >= kk (13 rr) scalars; fsh: 1024
+// floats of shared memory; ush: rr scalars of shared memory.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned peps_hash(unsigned a, unsigned b) {
+  unsigned h = a * 0x9E3779B1u ^ (b + 0x7F4A7C15u) * 0x85EBCA77u;
+  h ^= h >> 15; h *= 0x2C1B3C6Du; h ^= h >> 12; h *= 0x297A2D39u; h ^= h >> 15;
+  return h;
+}
+
+// number of singular values of the bidiagonal (d, e) below x (FP32)
+__device__ __forceinline__ int bidiag_count(const float* d, const float* e, int p, float x) {
+  const float x2 = x * x;
+  const float pivmin = 1e-36f;
+  float t = -x2;
+  int c = 0;
+  for (int i = 0; i < p; ++i) {
+    float D = d[i] * d[i] + t;
+    if (fabsf(D) < pivmin) D = -pivmin;
+    c += D < 0.0f;
+    if (i + 1 < p) t = t * (e[i] * e[i] / D) - x2;
+  }
+  return c;
+}
+
+template <class R>
+__device__ void svd_topk_rows(R* X, int rr, int n, int kk, R* VT, R* aux, R* inv,
+                              float* fsh, R* ush, double* red) {
+  typedef Arith<R> M;
+  const int t = threadIdx.x, nt = blockDim.x;
+  const int lane = t % PEPS_WARP, wid = t / PEPS_WARP, nw = (nt + PEPS_WARP - 1) / PEPS_WARP;
+  const int m = n, p = rr;
+  R* d = aux;
+  R* e = aux + p;
+  R* tau = aux + 2 * p;
+  R* sc = aux + 3 * p;  // scalars
+  // ---- 1. bidiagonalisation ---------------------------------------------
+  for (int k = 0; k < p; ++k) {
+    R* ck = X + (int64_t)k * n;
+    if (wid == 0) {
+      typename M::acc_t a;
+      M::acc_init(a);
+      for (int i = k + 1 + lane; i < m; i += PEPS_WARP) M::mac(a, ck[i], ck[i]);
+      R xn2 = warp_sum<R>(M::acc_get(a));
+      if (lane == 0) {
+        R alpha = ck[k];
+        if (!(M::to(xn2) > 0.0)) {
+          tau[k] = M::zero();
+          d[k] = alpha;
+        } else {
+          R nrm = M::sqrt_(alpha * alpha + xn2);
+          R beta = M::to(alpha) >= 0.0 ? -nrm : nrm;
+          tau[k] = (beta - alpha) / beta;
+          sc[0] = M::one() / (alpha - beta);
+          d[k] = beta;
+          ck[k] = beta;
+        }
+      }
+      __syncwarp();
+      if (M::to(tau[k]) != 0.0) {
+        const R scl = sc[0];
+        for (int i = k + 1 + lane; i < m; i += PEPS_WARP) ck[i] = ck[i] * scl;
+      }
+    }
+    __syncthreads();
+    const R tk = tau[k];
+    if (M::to(tk) != 0.0) {
+      for (int c = k + 1 + wid; c < p; c += nw) {
+        R* cc = X + (int64_t)c * n;
+        typename M::acc_t a;
+        M::acc_init(a);
+        if (lane == 0) M::mac(a, M::one(), cc[k]);
+        for (int i = k + 1 + lane; i < m; i += PEPS_WARP) M::mac(a, ck[i], cc[i]);
+        const R wv = tk * warp_sum<R>(M::acc_get(a));
+        if (lane == 0) cc[k] = cc[k] - wv;
+        for (int i = k + 1 + lane; i < m; i += PEPS_WARP) cc[i] = cc[i] - ck[i] * wv;
+      }
+    }
+    __syncthreads();
+    if (k + 1 < p) {
+      // row k of A over columns k+1..p-1: the entries X[c*n + k]
+      if (k + 2 < p) {
+        if (wid == 0) {
+          typename M::acc_t a;
+          M::acc_init(a);
+          for (int c = k + 2 + lane; c < p; c += PEPS_WARP) {
+            R x = X[(int64_t)c * n + k];
+            M::mac(a, x, x);
+          }
+          R xn2 = warp_sum<R>(M::acc_get(a));
+          if (lane == 0) {
+            R alpha = X[(int64_t)(k + 1) * n + k];
+            if (!(M::to(xn2) > 0.0)) {
+              sc[1] = M::zero();
+              e[k] = alpha;
+            } else {
+              R nrm = M::sqrt_(alpha * alpha + xn2);
+              R beta = M::to(alpha) >= 0.0 ? -nrm : nrm;
+              sc[1] = (beta - alpha) / beta;
+              sc[2] = M::one() / (alpha - beta);
+              e[k] = beta;
+              X[(int64_t)(k + 1) * n + k] = beta;
+            }
+          }
+          __syncwarp();
+          const bool on = M::to(sc[1]) != 0.0;
+          const R scl = sc[2];
+          for (int c = k + 1 + lane; c < p; c += PEPS_WARP) {
+            R u = M::one();
+            if (c > k + 1) {
+              u = on ? X[(int64_t)c * n + k] * scl : M::zero();
+              X[(int64_t)c * n + k] = u;
+            }
+            ush[c] = u;
+          }
+        }
+        __syncthreads();
+        const R tr = sc[1];
+        if (M::to(tr) != 0.0) {
+          for (int i = k + 1 + t; i < m; i += nt) {
+            typename M::acc_t a;
+            M::acc_init(a);
+            for (int c = k + 1; c < p; ++c) M::mac(a, ush[c], X[(int64_t)c * n + i]);
+            const R s = tr * M::acc_get(a);
+            for (int c = k + 1; c < p; ++c) X[(int64_t)c * n + i] = X[(int64_t)c * n + i] - ush[c] * s;
+          }
+        }
+        __syncthreads();
+      } else {
+        if (t == 0) e[k] = X[(int64_t)(k + 1) * n + k];
+        __syncthreads();
+      }
+    }
+  }
+  // ---- 2. singular values: FP32 bisection ---------------------------------
+  float* df = fsh;
+  float* ef = fsh + 256;
+  float* sg = fsh + 512;
+  double amax = 0.0;
+  for (int i = t; i < p; i += nt) {
+    amax = fmax(amax, fabs((double)M::hi(d[i])));
+    if (i + 1 < p) amax = fmax(amax, fabs((double)M::hi(e[i])));
+  }
+  const double smax = block_max(amax, red);
+  const float rs = smax > 0.0 ? (float)(1.0 / smax) : 0.0f;
+  for (int i = t; i < p; i += nt) {
+    df[i] = (float)M::hi(d[i]) * rs;
+    ef[i] = (i + 1 < p) ? (float)M::hi(e[i]) * rs : 0.0f;
+  }
+  __syncthreads();
+  for (int q = t; q < kk; q += nt) {
+    float bound = 0.0f;
+    for (int i = 0; i < p; ++i)
+      bound = fmaxf(bound, fabsf(df[i]) + fabsf(ef[i]) + (i > 0 ? fabsf(ef[i - 1]) : 0.0f));
+    const int idx = p - 1 - q;  // index from the smallest
+    float lo = 0.0f, hi = bound * 1.0001f + 1e-30f;
+    for (int it = 0; it < 200; ++it) {
+      float mid = (lo > 0.0f && hi > 4.0f * lo) ? sqrtf(lo) * sqrtf(hi) : 0.5f * (lo + hi);
+      if (mid <= 1e-30f) mid = 0.5f * (lo + hi);
+      if (bidiag_count(df, ef, p, mid) > idx) hi = mid; else lo = mid;
+      if (hi - lo <= 2e-7f * hi || hi < 1e-30f) break;
+    }
+    sg[q] = 0.5f * (lo + hi);  // in units of smax
+  }
+  __syncthreads();
+  // ---- 3. inverse iteration on the Golub-Kahan tridiagonal ----------------
+  const int N2 = 2 * p;
+  const int stride = 6 * N2 + p;
+  const float zero_tol = (float)(M::eps() * 4.0);
+  for (int q = t; q < kk; q += nt) {
+    R* U0 = inv + (int64_t)q * stride;
+    R* U1 = U0 + N2;
+    R* U2 = U1 + N2;
+    R* Lm = U2 + N2;
+    R* z = Lm + N2;
+    R* y = z + N2;
+    R* u = y + N2;
+    if (!(sg[q] > zero_tol)) {
+      for (int i = 0; i < p; ++i) u[i] = M::zero();
+      continue;
+    }
+    const R mu = M::from((double)sg[q] * smax);
+    const R tiny = M::from(smax * 1e-30 + 1e-300);
+    // g_j: off-diagonal j of the Golub-Kahan matrix
+#define PEPS_GK(j) (((j) & 1) ? e[(j) >> 1] : d[(j) >> 1])
+    R ca = -mu, cb = PEPS_GK(0), cc = M::zero();
+    for (int j = 0; j + 1 < N2; ++j) {
+      const R gs = PEPS_GK(j);
+      const R gn = (j + 2 < N2) ? PEPS_GK(j + 1) : M::zero();
+      const auto aa = fabs(M::hi(ca)), as = fabs(M::hi(gs));
+      if (aa >= as) {
+        R a0 = (aa == 0) ? tiny : ca;
+        R l = gs / a0;
+        U0[j] = a0; U1[j] = cb; U2[j] = cc; Lm[j] = l;
+        y[j] = M::zero();  // pivot flag 0
+        R na = -mu - l * cb;
+        R nb = gn - l * cc;
+        ca = na; cb = nb; cc = M::zero();
+      } else {
+        R l = ca / gs;
+        U0[j] = gs; U1[j] = -mu; U2[j] = gn; Lm[j] = l;
+        y[j] = M::one();  // pivot flag 1
+        R na = cb + l * mu;
+        R nb = cc - l * gn;
+        ca = na; cb = nb; cc = M::zero();
+      }
+    }
+    U0[N2 - 1] = (M::hi(ca) == 0) ? tiny : ca;
+    U1[N2 - 1] = M::zero();
+    U2[N2 - 1] = M::zero();
+    // the pivot flags were staged in y: move them to z, y becomes the rhs
+    for (int j = 0; j + 1 < N2; ++j) z[j] = y[j];
+    // start vector
+    for (int j = 0; j < N2; ++j)
+      y[j] = M::from(1.0 + (double)(peps_hash((unsigned)q, (unsigned)j) & 0xffff) * (1.0 / 65536.0));
+    for (int iter = 0; iter < 3; ++iter) {
+      // forward: row interchanges and eliminations
+      for (int j = 0; j + 1 < N2; ++j) {
+        if (M::hi(z[j]) != 0) { R tmp = y[j]; y[j] = y[j + 1]; y[j + 1] = tmp; }
+        y[j + 1] = y[j + 1] - Lm[j] * y[j];
+      }
+      // back substitution
+      R x1 = M::zero(), x2 = M::zero();
+      double ymax = 0.0;
+      for (int j = N2 - 1; j >= 0; --j) {
+        R xj = (y[j] - U1[j] * x1 - U2[j] * x2) / U0[j];
+        y[j] = xj;
+        x2 = x1;
+        x1 = xj;
+        ymax = fmax(ymax, fabs((double)M::hi(xj)));
+      }
+      // scale to unit max-abs before the norm (the squares could leave the
+      // FP32 exponent range in the float-float form), then to unit norm
+      const R r0 = M::from(ymax > 0.0 ? 1.0 / ymax : 1.0);
+      typename M::acc_t nrm;
+      M::acc_init(nrm);
+      for (int j = 0; j < N2; ++j) {
+        y[j] = y[j] * r0;
+        M::mac(nrm, y[j], y[j]);
+      }
+      const R s = M::one() / M::sqrt_(M::acc_get(nrm));
+      for (int j = 0; j < N2; ++j) y[j] = y[j] * s;
+    }
+    for (int i = 0; i < p; ++i) u[i] = y[2 * i + 1];
+#undef PEPS_GK
+  }
+  __syncthreads();
+  // ---- 4a. Gram-Schmidt on the u's (in order of decreasing sigma) --------
+  for (int q = 0; q < kk; ++q) {
+    R* uq = inv + (int64_t)q * stride + 6 * N2;
+    if (!(sg[q] > zero_tol)) continue;  // zero row
+    for (int pass = 0; pass < 2; ++pass) {
+      // coefficients against the earlier vectors (warp per vector)
+      for (int r = wid; r < q; r += nw) {
+        const R* ur = inv + (int64_t)r * stride + 6 * N2;
+        typename M::acc_t a;
+        M::acc_init(a);
+        for (int i = lane; i < p; i += PEPS_WARP) M::mac(a, ur[i], uq[i]);
+        R cf = warp_sum<R>(M::acc_get(a));
+        if (lane == 0) ush[r] = (sg[r] > zero_tol) ? cf : M::zero();
+      }
+      __syncthreads();
+      for (int i = t; i < p; i += nt) {
+        R v = uq[i];
+        for (int r = 0; r < q; ++r) v = v - ush[r] * (inv + (int64_t)r * stride + 6 * N2)[i];
+        uq[i] = v;
+      }
+      __syncthreads();
+    }
+    typename M::acc_t a;
+    M::acc_init(a);
+    for (int i = t; i < p; i += nt) M::mac(a, uq[i], uq[i]);
+    R n2 = block_sum<R>(M::acc_get(a), reinterpret_cast<R*>(red));
+    const R s = (M::to(n2) > 0.0) ? M::one() / M::sqrt_(n2) : M::zero();
+    for (int i = t; i < p; i += nt) uq[i] = uq[i] * s;
+    __syncthreads();
+  }
+  // ---- 4b. V_i = Q [u_i; 0] (reflectors in reverse order), one warp each --
+  for (int q = wid; q < kk; q += nw) {
+    R* v = VT + (int64_t)q * n;
+    const R* uq = inv + (int64_t)q * stride + 6 * N2;
+    for (int i = lane; i < n; i += PEPS_WARP) v[i] = (i < p) ? uq[i] : M::zero();
+    __syncwarp();
+    if (!(sg[q] > zero_tol)) continue;
+    for (int k = p - 1; k >= 0; --k) {
+      const R tk = tau[k];
+      if (M::to(tk) == 0.0) continue;
+      const R* ck = X + (int64_t)k * n;
+      typename M::acc_t a;
+      M::acc_init(a);
+      if (lane == 0) M::mac(a, M::one(), v[k]);
+      for (int i = k + 1 + lane; i < n; i += PEPS_WARP) M::mac(a, ck[i], v[i]);
+      const R s = tk * warp_sum<R>(M::acc_get(a));
+      __syncwarp();
+      if (lane == 0) v[k] = v[k] - s;
+      for (int i = k + 1 + lane; i < n; i += PEPS_WARP) v[i] = v[i] - ck[i] * s;
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+}

@@ -31,6 +31,7 @@ __device__ Work<R> make_work(const PepsPlan& P, R* ws, double* wsd, int slot) {
   w.scl = bd + P.doff_scale;
   w.delta = bd + P.doff_delta;
   w.alpha = base + P.off_alpha;
+  w.inv = base + P.off_inv;
   return w;
 }
 

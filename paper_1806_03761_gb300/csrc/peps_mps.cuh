@@ -32,7 +32,8 @@ struct Work {
   R* r2;
   double* scl;    // log-scales of the strip envs: 4 (L+1)
   double* delta;  // staged Delta of one sample: N D^4
-  R* alpha;       // Jacobi row norms
+  R* alpha;       // singular-value scratch (d, e, tau of the bidiagonal)
+  R* inv;         // inverse-iteration scratch
   // shared memory
   double* red;
   R* redR;
@@ -175,11 +176,12 @@ __device__ double compress_row(const PepsPlan& P, const PepsStep& st, bool above
     const int kk = st.oa[j];
     R* V = Mout + (int64_t)j * SC;  // V^T (kk x n) is the truncated site j
     normalize_pow2<R>(w.xj, rr * n, w.red);
+    float* fsh = reinterpret_cast<float*>(w.rot);
     if (rr > n) {
       householder_r<R>(w.xj, rr, n, w.b2, w.wsh);
-      jacobi_rows<R>(w.b2, n, n, kk, V, w.alpha, w.ish, w.red, w.flags);
+      svd_topk_rows<R>(w.b2, n, n, kk, V, w.alpha, w.inv, fsh, w.wsh, w.red);
     } else {
-      jacobi_rows<R>(w.xj, rr, n, kk, V, w.alpha, w.ish, w.red, w.flags);
+      svd_topk_rows<R>(w.xj, rr, n, kk, V, w.alpha, w.inv, fsh, w.wsh, w.red);
     }
     // C_j[(a,l)][k] = sum_{(q,c)} Y[(a,l)][(q,c)] V^T[k][(q,c)]
     c = ctr_init();

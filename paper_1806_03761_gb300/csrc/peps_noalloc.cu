@@ -135,7 +135,8 @@ void plan_fp64(const peps_shape& s, PepsPlan* P, NoallocSteps* steps) {
   P->off_r1 = take((int64_t)(L + 1) * P->site_cap);
   P->off_l2 = 0;  // the two-row strip is not used by this entry point
   P->off_r2 = 0;
-  P->off_alpha = take((int64_t)Dc * D + 8);
+  P->off_alpha = take(3 * (int64_t)Dc * D + 16);
+  P->off_inv = take(13 * (int64_t)Dc * Dc * D);
   P->off_tmp = take(32);
   P->slot_elems = o;
   int64_t d = 0;

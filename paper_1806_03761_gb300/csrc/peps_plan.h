@@ -39,7 +39,7 @@ struct PepsPlan {
   int64_t env2_cap;   // Dc*D*D*Dc: two-row strip environment
   // per-slot workspace offsets in scalars of the form's type
   int64_t off_dn, off_up, off_rst, off_b0, off_b1, off_b2, off_y, off_xj,
-      off_vt, off_c0, off_c1, off_l1, off_r1, off_l2, off_r2, off_alpha, off_tmp;
+      off_vt, off_c0, off_c1, off_l1, off_r1, off_l2, off_r2, off_alpha, off_inv, off_tmp;
   int64_t slot_elems;  // scalars per slot
   // per-slot workspace offsets in doubles
   int64_t doff_scale, doff_delta, doff_alpha;
