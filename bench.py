@@ -286,8 +286,7 @@ def main():
     ms = total_ms / max(args.steps, 1)
     value = B * world / (ms / 1e3)
     # roofline of the dominant kernel (the evaluation kernel)
-    sweeps = float(os.environ.get("PEPS_JACOBI_SWEEPS", "9"))
-    flops = P.flops_per_sample(L, D, Dc, jacobi_sweeps=sweeps, precision=args.precision)
+    flops = P.flops_per_sample(L, D, Dc, precision=args.precision)
     ev = float(np.mean(eval_ms)) if eval_ms else float("nan")
     achieved = flops * B / (ev / 1e3) / 1e12
     sm_max = clk.get("sm_max_mhz") or 2070.0

@@ -211,9 +211,10 @@ int peps_sync_status(peps_ctx* ctx, void* stream, int32_t* flags);
 
 /* Algorithmic floating-point operation count of one sample of
  * peps_evaluate (energy + log-derivatives) under this shape, as the kernels
- * perform it (contractions, QR, and Jacobi at `jacobi_sweeps` sweeps); host
- * call used for roofline reporting. */
-double peps_flops_per_sample(const peps_shape* shape, double jacobi_sweeps);
+ * perform it (contractions, Householder QR, bidiagonalisation, inverse
+ * iteration, back-transformation; multiply-adds count 2); host call used for
+ * roofline reporting.  0 for an invalid shape. */
+double peps_flops_per_sample(const peps_shape* shape);
 
 #ifdef __cplusplus
 }

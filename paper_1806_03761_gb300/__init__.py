@@ -36,9 +36,10 @@ def workspace_bytes(L, D, Dc, precision="fp64", slots=0, J1=1.0, J2=0.5):
     return int(_lib.load().peps_workspace_bytes(ctypes.byref(s), int(slots)))
 
 
-def flops_per_sample(L, D, Dc, jacobi_sweeps=8.0, precision="fp64"):
+def flops_per_sample(L, D, Dc, precision="fp64"):
+    """Algorithmic flops of one sample of peps_evaluate (host call)."""
     s = _shape(L, D, Dc, 1.0, 0.5, precision)
-    return float(_lib.load().peps_flops_per_sample(ctypes.byref(s), float(jacobi_sweeps)))
+    return float(_lib.load().peps_flops_per_sample(ctypes.byref(s)))
 
 
 def _ptr(t):

@@ -56,7 +56,7 @@ _SIGS = {
     "peps_grad_step": (I32, [P, P, P, P, I64, F64, U64, U64, P, P]),
     "peps_sample_batch": (I32, [P, U64, I64, I64, I32, I32, I32, U64, P, P, P, P]),
     "peps_sync_status": (I32, [P, P, ctypes.POINTER(I32)]),
-    "peps_flops_per_sample": (F64, [ctypes.POINTER(PepsShape), F64]),
+    "peps_flops_per_sample": (F64, [ctypes.POINTER(PepsShape)]),
     "peps_amplitudes_noalloc": (I32, [ctypes.POINTER(PepsShape), P, P, I64, P, P, P]),
 }
 

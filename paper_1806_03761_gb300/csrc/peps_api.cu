@@ -417,7 +417,7 @@ int peps_sync_status(peps_ctx* c, void* stream, int32_t* flags) {
   return PEPS_OK;
 }
 
-double peps_flops_per_sample(const peps_shape* shape, double jacobi_sweeps) {
+double peps_flops_per_sample(const peps_shape* shape) {
   std::string why;
   if (!shape_ok(shape, &why)) return 0.0;
   PepsPlan P;
@@ -428,7 +428,6 @@ double peps_flops_per_sample(const peps_shape* shape, double jacobi_sweeps) {
   // environments: both directions, every step
   for (int dir = 0; dir < 2; ++dir)
     for (int t = 0; t < L - 1; ++t) {
-      if (dir == 1 && t == L - 2) continue;  // U_{L-2} is built but Dn_0 is not
       const PepsStep& st = steps[t];
       int rprev = 1;
       for (int j = 0; j < L - 1; ++j) {
@@ -448,12 +447,15 @@ double peps_flops_per_sample(const peps_shape* shape, double jacobi_sweeps) {
         f += 2.0 * a * p * Dr * cn * b;               // S2
         f += 2.0 * a * Dl * D * cn * p * Dr;          // Y
         if (j == 0) break;
-        double rr = st.r[j - 1], n = (double)D * cn, A = a * Dl;
+        double rr = st.r[j - 1], n = (double)D * cn, A = a * Dl, kk = st.oa[j];
         f += 2.0 * rr * n * A;                        // X_j = R Y
-        double r2 = std::min(rr, n);
         if (rr > n) f += 2.0 * rr * n * n - (2.0 / 3.0) * n * n * n;
-        f += jacobi_sweeps * (r2 * (r2 - 1) / 2.0) * (2.0 * n + 6.0 * n);  // dots + rotations
-        f += 2.0 * A * st.oa[j] * n;                  // C_j
+        double q = std::min(rr, n);
+        f += 4.0 * n * q * q - (4.0 / 3.0) * q * q * q;  // bidiagonalisation
+        f += kk * 80.0 * q;                           // inverse iteration
+        f += 2.0 * kk * kk * q;                       // Gram-Schmidt
+        f += kk * (4.0 * n * q - 2.0 * q * q);        // back-transformation
+        f += 2.0 * A * kk * n;                        // C_j
         cn = st.oa[j];
       }
     }

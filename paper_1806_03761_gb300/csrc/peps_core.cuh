@@ -10,7 +10,9 @@
 #include "peps_arith.cuh"
 #include "peps_plan.h"
 
+#ifndef PEPS_NT
 #define PEPS_NT 256          // threads per block
+#endif
 #ifndef PEPS_WARP
 #define PEPS_WARP 32         // lanes per warp
 #endif
@@ -88,25 +90,41 @@ __device__ __forceinline__ Ctr ctr_init() {
 template <class R>
 __device__ void contract(const Ctr& d, const R* A, const R* B, R* C) {
   typedef Arith<R> M;
-  const int tot = d.e[0] * d.e[1] * d.e[2] * d.e[3] * d.e[4];
+  // each thread computes two outputs adjacent in the fastest digit (two
+  // independent accumulations, shared loads where an operand does not carry
+  // that digit)
+  const int e4 = d.e[4];
+  const int h4 = (e4 + 1) >> 1;
+  const int tot = d.e[0] * d.e[1] * d.e[2] * d.e[3] * h4;
+  const int sa4 = d.sa[4], sb4 = d.sb[4], sc4 = d.sc[4];
   for (int o = threadIdx.x; o < tot; o += blockDim.x) {
     int t = o;
-    int i4 = t % d.e[4]; t /= d.e[4];
-    int i3 = t % d.e[3]; t /= d.e[3];
-    int i2 = t % d.e[2]; t /= d.e[2];
-    int i1 = t % d.e[1];
-    int i0 = t / d.e[1];
-    int oa = i0 * d.sa[0] + i1 * d.sa[1] + i2 * d.sa[2] + i3 * d.sa[3] + i4 * d.sa[4];
-    int ob = i0 * d.sb[0] + i1 * d.sb[1] + i2 * d.sb[2] + i3 * d.sb[3] + i4 * d.sb[4];
-    int oc = i0 * d.sc[0] + i1 * d.sc[1] + i2 * d.sc[2] + i3 * d.sc[3] + i4 * d.sc[4];
-    typename M::acc_t acc;
-    M::acc_init(acc);
+    const int i4 = 2 * (t % h4); t /= h4;
+    const int i3 = t % d.e[3]; t /= d.e[3];
+    const int i2 = t % d.e[2]; t /= d.e[2];
+    const int i1 = t % d.e[1];
+    const int i0 = t / d.e[1];
+    const bool two = i4 + 1 < e4;
+    const int oa = i0 * d.sa[0] + i1 * d.sa[1] + i2 * d.sa[2] + i3 * d.sa[3] + i4 * sa4;
+    const int ob = i0 * d.sb[0] + i1 * d.sb[1] + i2 * d.sb[2] + i3 * d.sb[3] + i4 * sb4;
+    const int oc = i0 * d.sc[0] + i1 * d.sc[1] + i2 * d.sc[2] + i3 * d.sc[3] + i4 * sc4;
+    const int da = two ? sa4 : 0, db = two ? sb4 : 0;
+    typename M::acc_t acc0, acc1;
+    M::acc_init(acc0);
+    M::acc_init(acc1);
     for (int k1 = 0; k1 < d.k1; ++k1) {
       const R* pa = A + oa + k1 * d.ka1;
       const R* pb = B + ob + k1 * d.kb1;
-      for (int k2 = 0; k2 < d.k2; ++k2) M::mac(acc, pa[k2 * d.ka2], pb[k2 * d.kb2]);
+      for (int k2 = 0; k2 < d.k2; ++k2) {
+        const R a0 = pa[k2 * d.ka2], b0 = pb[k2 * d.kb2];
+        const R a1 = da ? pa[k2 * d.ka2 + da] : a0;
+        const R b1 = db ? pb[k2 * d.kb2 + db] : b0;
+        M::mac(acc0, a0, b0);
+        M::mac(acc1, a1, b1);
+      }
     }
-    C[oc] = M::acc_get(acc);
+    C[oc] = M::acc_get(acc0);
+    if (two) C[oc + sc4] = M::acc_get(acc1);
   }
   __syncthreads();
 }
@@ -126,6 +144,44 @@ __device__ double normalize_pow2(R* x, int n, double* red) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = x[i] * rs;
   __syncthreads();
   return (double)e * 0.69314718055994530942;
+}
+
+// Apply H = I - tau w w^T (w = e_k + the stored tail xk[k+1..m-1]) to the
+// columns c0..c1-1 of the column-major X (ld m), two columns per warp.
+template <class R>
+__device__ __forceinline__ void reflect_columns(R* X, int m, int k, int c0, int c1,
+                                                const R* xk, R tau) {
+  typedef Arith<R> M;
+  const int lane = threadIdx.x % PEPS_WARP, wid = threadIdx.x / PEPS_WARP;
+  const int nw = (blockDim.x + PEPS_WARP - 1) / PEPS_WARP;
+  for (int c = c0 + 2 * wid; c < c1; c += 2 * nw) {
+    const bool two = c + 1 < c1;
+    R* xa = X + (int64_t)c * m;
+    R* xb = two ? xa + m : xa;
+    typename M::acc_t a, b;
+    M::acc_init(a);
+    M::acc_init(b);
+    if (lane == 0) {
+      M::mac(a, M::one(), xa[k]);
+      M::mac(b, M::one(), xb[k]);
+    }
+    for (int i = k + 1 + lane; i < m; i += PEPS_WARP) {
+      const R v = xk[i];
+      M::mac(a, v, xa[i]);
+      M::mac(b, v, xb[i]);
+    }
+    const R wa = tau * warp_sum<R>(M::acc_get(a));
+    const R wb = tau * warp_sum<R>(M::acc_get(b));
+    if (lane == 0) {
+      xa[k] = xa[k] - wa;
+      if (two) xb[k] = xb[k] - wb;
+    }
+    for (int i = k + 1 + lane; i < m; i += PEPS_WARP) {
+      const R v = xk[i];
+      xa[i] = xa[i] - v * wa;
+      if (two) xb[i] = xb[i] - v * wb;
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -167,18 +223,7 @@ __device__ void householder_r(R* X, int m, int n, R* Rout, R* sh) {
     }
     __syncthreads();
     const R tau = sh[0];
-    if (M::to(tau) != 0.0) {
-      for (int c = k + 1 + wid; c < n; c += nw) {
-        R* xc = X + (int64_t)c * m;
-        typename M::acc_t a;
-        M::acc_init(a);
-        if (lane == 0) M::mac(a, M::one(), xc[k]);
-        for (int i = k + 1 + lane; i < m; i += PEPS_WARP) M::mac(a, xk[i], xc[i]);
-        R wv = tau * warp_sum<R>(M::acc_get(a));
-        if (lane == 0) xc[k] = xc[k] - wv;
-        for (int i = k + 1 + lane; i < m; i += PEPS_WARP) xc[i] = xc[i] - xk[i] * wv;
-      }
-    }
+    if (M::to(tau) != 0.0) reflect_columns<R>(X, m, k, k + 1, n, xk, tau);
     __syncthreads();
   }
   for (int o = t; o < kmax * n; o += blockDim.x) {
@@ -407,18 +452,7 @@ __device__ void svd_topk_rows(R* X, int rr, int n, int kk, R* VT, R* aux, R* inv
     }
     __syncthreads();
     const R tk = tau[k];
-    if (M::to(tk) != 0.0) {
-      for (int c = k + 1 + wid; c < p; c += nw) {
-        R* cc = X + (int64_t)c * n;
-        typename M::acc_t a;
-        M::acc_init(a);
-        if (lane == 0) M::mac(a, M::one(), cc[k]);
-        for (int i = k + 1 + lane; i < m; i += PEPS_WARP) M::mac(a, ck[i], cc[i]);
-        const R wv = tk * warp_sum<R>(M::acc_get(a));
-        if (lane == 0) cc[k] = cc[k] - wv;
-        for (int i = k + 1 + lane; i < m; i += PEPS_WARP) cc[i] = cc[i] - ck[i] * wv;
-      }
-    }
+    if (M::to(tk) != 0.0) reflect_columns<R>(X, n, k, k + 1, p, ck, tk);
     __syncthreads();
     if (k + 1 < p) {
       // row k of A over columns k+1..p-1: the entries X[c*n + k]
@@ -461,11 +495,17 @@ __device__ void svd_topk_rows(R* X, int rr, int n, int kk, R* VT, R* aux, R* inv
         const R tr = sc[1];
         if (M::to(tr) != 0.0) {
           for (int i = k + 1 + t; i < m; i += nt) {
-            typename M::acc_t a;
+            typename M::acc_t a, b;
             M::acc_init(a);
-            for (int c = k + 1; c < p; ++c) M::mac(a, ush[c], X[(int64_t)c * n + i]);
-            const R s = tr * M::acc_get(a);
-            for (int c = k + 1; c < p; ++c) X[(int64_t)c * n + i] = X[(int64_t)c * n + i] - ush[c] * s;
+            M::acc_init(b);
+            int c = k + 1;
+            for (; c + 1 < p; c += 2) {
+              M::mac(a, ush[c], X[(int64_t)c * n + i]);
+              M::mac(b, ush[c + 1], X[(int64_t)(c + 1) * n + i]);
+            }
+            if (c < p) M::mac(a, ush[c], X[(int64_t)c * n + i]);
+            const R s = tr * (M::acc_get(a) + M::acc_get(b));
+            for (c = k + 1; c < p; ++c) X[(int64_t)c * n + i] = X[(int64_t)c * n + i] - ush[c] * s;
           }
         }
         __syncthreads();

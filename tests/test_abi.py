@@ -51,8 +51,9 @@ def test_workspace_and_flop_model_host_only(lib):
     n1 = p.workspace_bytes(16, 6, 24, "fp64", slots=1)
     n2 = p.workspace_bytes(16, 6, 24, "fp64", slots=2)
     assert n2 > n1 > 10 * 2 ** 20
-    f = p.flops_per_sample(16, 6, 24, jacobi_sweeps=8)
+    f = p.flops_per_sample(16, 6, 24)
     assert 1e10 < f < 5e11
+    assert p.flops_per_sample(1, 6, 24) == 0.0
     assert p.workspace_bytes(1, 6, 24) == 0  # bad shape
     assert p.workspace_bytes(16, 6, 100) == 0  # Dc*D > 256
 
