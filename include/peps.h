@@ -27,7 +27,7 @@
  *     enqueue work on it and return; results are ready when the stream is.
  *   - Return value: PEPS_OK or a negative PEPS_E* code; peps_last_error()
  *     gives a message.  No C++ exception crosses this ABI.  Errors found on the
- *     device (non-finite input, zero amplitude, a Jacobi sweep limit) are
+ *     device (non-finite input, zero amplitude) are
  *     recorded in the context and returned by peps_sync_status().
  *   - One context per host thread at a time; calls on one context must not
  *     overlap on the device (they share the context's workspace).
@@ -47,7 +47,7 @@ enum {
   PEPS_EINVAL = -1,   /* bad argument (NULL, size, alignment, shape) */
   PEPS_ENOMEM = -2,   /* device allocation failed */
   PEPS_ECUDA = -3,    /* CUDA runtime error (launch, copy, no device) */
-  PEPS_ENUMERIC = -4, /* non-finite input, zero amplitude, no convergence */
+  PEPS_ENUMERIC = -4, /* non-finite input or zero amplitude */
   PEPS_ETIMEOUT = -5, /* a bounded device wait ran out */
   PEPS_ESCRATCH = -6  /* peps_amplitudes_noalloc: the shape does not fit the
                          fixed device scratch */
@@ -69,7 +69,7 @@ enum {
 enum {
   PEPS_FLAG_NONFINITE = 1,   /* NaN/Inf met in a tensor or ratio */
   PEPS_FLAG_ZERO_AMP = 2,    /* W(S) = 0 for some sample (its sign is 0) */
-  PEPS_FLAG_NO_CONVERGE = 4  /* a Jacobi SVD hit its sweep limit */
+  PEPS_FLAG_NO_CONVERGE = 4  /* reserved */
 };
 
 typedef struct peps_ctx peps_ctx;

@@ -1,7 +1,6 @@
 // peps_core.cuh -- thread-block building blocks of the per-sample PEPS
-// contraction (PEPS++, arXiv:1806.03761): strided tensor contractions,
-// Householder QR, one-sided Jacobi SVD, boundary-MPS absorption with
-// truncation, and the one- and two-row strips.
+// contraction (PEPS++, arXiv:1806.03761): reductions, strided tensor
+// contractions, Householder QR and the truncated SVD of the bond matrices.
 //
 // Every routine is executed by all threads of one thread block on the
 // workspace of one sample; it ends with __syncthreads() so its result can be
@@ -16,7 +15,6 @@
 #ifndef PEPS_WARP
 #define PEPS_WARP 32         // lanes per warp
 #endif
-#define PEPS_JACOBI_MAXSWEEP 40
 
 // ---------------------------------------------------------------------------
 // Warp- and block-wide reductions (warp shuffles, one shared slot per warp).
@@ -133,9 +131,10 @@ __device__ void contract(const Ctr& d, const R* A, const R* B, R* C) {
 // the natural log of the factor removed (0 for an all-zero x).
 template <class R>
 __device__ double normalize_pow2(R* x, int n, double* red) {
-  double m = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, fabs(Arith<R>::to(x[i])));
-  m = block_max(m, red);
+  // the leading part decides the power of two (no FP64 work per element)
+  decltype(Arith<R>::hi(R())) mh = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) mh = fmax(mh, fabs(Arith<R>::hi(x[i])));
+  double m = block_max((double)mh, red);
   if (!(m > 0.0) || !isfinite(m)) return 0.0;
   int e;
   frexp(m, &e);  // m = f 2^e, f in [1/2, 1)
@@ -188,14 +187,16 @@ __device__ __forceinline__ void reflect_columns(R* X, int m, int k, int c0, int 
 // Householder QR, R factor only (LAPACK-style reflectors H = I - tau v v^T,
 // v_k = 1).  X is m x n COLUMN-major (X[c*m + i]), overwritten.  The first
 // min(m,n) rows of R are written row-major to Rout (ld n), zeros below the
-// diagonal.  Warp 0 forms each reflector; then one warp per column applies
-// it (dot product and update over contiguous rows).
+// diagonal.  Warp 0 forms each reflector; then it is applied to the columns
+// on its right, two columns per warp.  (A blocked compact-WY variant was
+// measured: about 20 % faster in isolation in float-float, slower in FP64,
+// and its accumulator arrays made the fused kernel spill registers.)
+// sh: >= 2 scalars of shared memory.
 // ---------------------------------------------------------------------------
 template <class R>
 __device__ void householder_r(R* X, int m, int n, R* Rout, R* sh) {
   typedef Arith<R> M;
-  const int t = threadIdx.x, lane = t % PEPS_WARP, wid = t / PEPS_WARP,
-            nw = (blockDim.x + PEPS_WARP - 1) / PEPS_WARP;
+  const int t = threadIdx.x, lane = t % PEPS_WARP, wid = t / PEPS_WARP;
   const int kmax = m < n ? m : n;
   for (int k = 0; k < kmax; ++k) {
     R* xk = X + (int64_t)k * m;
@@ -206,11 +207,11 @@ __device__ void householder_r(R* X, int m, int n, R* Rout, R* sh) {
       R xn2 = warp_sum<R>(M::acc_get(a));
       if (lane == 0) {
         R alpha = xk[k];
-        if (!(M::to(xn2) > 0.0)) {
+        if (!(M::hi(xn2) > 0)) {
           sh[0] = M::zero();  // tau = 0: H = I
         } else {
           R nrm = M::sqrt_(alpha * alpha + xn2);
-          R beta = M::to(alpha) >= 0.0 ? -nrm : nrm;
+          R beta = M::hi(alpha) >= 0 ? -nrm : nrm;
           sh[0] = (beta - alpha) / beta;
           sh[1] = M::one() / (alpha - beta);
           xk[k] = beta;
@@ -218,12 +219,12 @@ __device__ void householder_r(R* X, int m, int n, R* Rout, R* sh) {
       }
       __syncwarp();
       R tau = sh[0], scl = sh[1];
-      if (M::to(tau) != 0.0)
+      if (M::hi(tau) != 0)
         for (int i = k + 1 + lane; i < m; i += PEPS_WARP) xk[i] = xk[i] * scl;
     }
     __syncthreads();
     const R tau = sh[0];
-    if (M::to(tau) != 0.0) reflect_columns<R>(X, m, k, k + 1, n, xk, tau);
+    if (M::hi(tau) != 0) reflect_columns<R>(X, m, k, k + 1, n, xk, tau);
     __syncthreads();
   }
   for (int o = t; o < kmax * n; o += blockDim.x) {
@@ -231,143 +232,6 @@ __device__ void householder_r(R* X, int m, int n, R* Rout, R* sh) {
     Rout[o] = (c >= i) ? X[(int64_t)c * m + i] : M::zero();
   }
   __syncthreads();
-}
-
-// ---------------------------------------------------------------------------
-// One-sided (Hestenes) Jacobi on the ROWS of X (rr x n, rr <= n, ld n):
-// rotations of row pairs until all rows are mutually orthogonal; the rows
-// are then sigma_i v_i^T with v_i the right singular vectors of X.  Writes
-// the kk rows of largest norm, normalised, to VT (kk x n) in decreasing
-// order (zero rows for zero singular values).  Pairs are visited in the
-// round-robin (circle) order; the rr/2 disjoint pairs of a round are spread
-// over groups of PEPS_JG lanes (dot product, rotation and update inside the
-// group), with one barrier per round.  The rotation is computed in the
-// form's own arithmetic.  Rows whose squared norm is below eps^2 times the
-// largest are left alone (their singular values are below rounding level).
-// alpha: rr scalars of scratch.  Returns the number of sweeps used.
-// ---------------------------------------------------------------------------
-#ifndef PEPS_JG
-#define PEPS_JG (PEPS_WARP >= 8 ? 8 : PEPS_WARP)  // lanes per rotation pair
-#endif
-
-__device__ __forceinline__ int rr_player(int pos, int rd, int rp) {
-  return pos == 0 ? 0 : ((pos - 1 + rd) % (rp - 1)) + 1;
-}
-
-template <class R>
-__device__ __forceinline__ R group_sum(R v) {
-  for (int o = PEPS_JG / 2; o > 0; o >>= 1) v = v + shfl_xor_r(v, o);
-  return v;
-}
-
-template <class R>
-__device__ void row_norms(const R* X, int rr, int n, R* alpha) {
-  typedef Arith<R> M;
-  const int g = threadIdx.x / PEPS_JG, gl = threadIdx.x % PEPS_JG;
-  const int ng = blockDim.x / PEPS_JG;
-  for (int base = 0; base < rr; base += ng) {
-    const int p = base + g;
-    typename M::acc_t a;
-    M::acc_init(a);
-    if (p < rr)
-      for (int e = gl; e < n; e += PEPS_JG) M::mac(a, X[p * n + e], X[p * n + e]);
-    R s = group_sum<R>(M::acc_get(a));
-    if (p < rr && gl == 0) alpha[p] = s;
-  }
-  __syncthreads();
-}
-
-template <class R>
-__device__ int jacobi_rows(R* X, int rr, int n, int kk, R* VT, R* alpha,
-                           int* shi, double* red, int* flags) {
-  typedef Arith<R> M;
-  const int t = threadIdx.x;
-  const int g = t / PEPS_JG, gl = t % PEPS_JG, ng = blockDim.x / PEPS_JG;
-  const int rp = rr + (rr & 1);
-  const int npair = rp / 2;
-  const double tol = (double)n * M::eps();
-  row_norms<R>(X, rr, n, alpha);
-  int sweep = 0;
-  for (; sweep < PEPS_JACOBI_MAXSWEEP && rr > 1; ++sweep) {
-    double amax = 0.0;
-    for (int p = t; p < rr; p += blockDim.x) amax = fmax(amax, (double)M::hi(alpha[p]));
-    const double thr = block_max(amax, red) * M::eps() * M::eps();
-    if (t == 0) shi[0] = 0;
-    __syncthreads();
-    for (int rd = 0; rd < rp - 1; ++rd) {
-      for (int base = 0; base < npair; base += ng) {
-        const int pr = base + g;
-        int pp = rr, qq = rr;
-        if (pr < npair) { pp = rr_player(pr, rd, rp); qq = rr_player(rp - 1 - pr, rd, rp); }
-        const bool live = pp < rr && qq < rr;
-        R* xp = X + (live ? pp : 0) * n;
-        R* xq = X + (live ? qq : 0) * n;
-        typename M::acc_t a;
-        M::acc_init(a);
-        if (live)
-          for (int e = gl; e < n; e += PEPS_JG) M::mac(a, xp[e], xq[e]);
-        const R gam = group_sum<R>(M::acc_get(a));  // every lane of the group
-        if (!live) continue;
-        const R ap = alpha[pp], aq = alpha[qq];
-        const double gh = (double)M::hi(gam), aph = (double)M::hi(ap), aqh = (double)M::hi(aq);
-        if (aph > thr && aqh > thr && gh * gh > tol * tol * aph * aqh) {
-          // zeta = (a_q - a_p) / (2 gamma); t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2))
-          const R zeta = (aq - ap) / (gam + gam);
-          const R az = M::hi(zeta) >= 0 ? zeta : -zeta;
-          // for |zeta| > 2^50, sqrt(1 + zeta^2) = |zeta| to working precision
-          // (and zeta^2 could leave the FP32 exponent range)
-          R tt = (double)M::hi(az) > 1.125899906842624e15
-                     ? M::one() / (az + az)
-                     : M::one() / (az + M::sqrt_(M::one() + zeta * zeta));
-          if (M::hi(zeta) < 0) tt = -tt;
-          const R c = M::one() / M::sqrt_(M::one() + tt * tt);
-          const R s = c * tt;
-          for (int e = gl; e < n; e += PEPS_JG) {
-            R u = xp[e], v = xq[e];
-            xp[e] = c * u - s * v;
-            xq[e] = s * u + c * v;
-          }
-          if (gl == 0) {
-            alpha[pp] = ap - tt * gam;
-            alpha[qq] = aq + tt * gam;
-            shi[0] = 1;
-          }
-        }
-      }
-      __syncthreads();
-    }
-    const int any = shi[0];
-    row_norms<R>(X, rr, n, alpha);
-    if (!any) break;
-  }
-  if (sweep >= PEPS_JACOBI_MAXSWEEP && t == 0) atomicOr(flags, 4);
-  // Rows at or below the threshold were never orthogonalised: they stand
-  // for singular values below eps * sigma_max and are written as zero rows,
-  // so that V^T V stays the projector onto an orthonormal kept subspace.
-  double amax = 0.0;
-  for (int p = t; p < rr; p += blockDim.x) amax = fmax(amax, (double)M::hi(alpha[p]));
-  const double thr = block_max(amax, red) * M::eps() * M::eps();
-  // rank rows by norm (ties by index) and write the kk largest, normalised
-  for (int p = t; p < rr; p += blockDim.x) {
-    int rank = 0;
-    const double ap = M::to(alpha[p]);
-    for (int q = 0; q < rr; ++q) {
-      const double aq = M::to(alpha[q]);
-      rank += (aq > ap) || (aq == ap && q < p);
-    }
-    shi[1 + p] = rank;
-  }
-  __syncthreads();
-  for (int o = t; o < kk * n; o += blockDim.x) VT[o] = M::zero();
-  __syncthreads();
-  for (int o = t; o < rr * n; o += blockDim.x) {
-    int p = o / n, e = o % n;
-    int rank = shi[1 + p];
-    if (rank < kk && (double)M::hi(alpha[p]) > thr)
-      VT[rank * n + e] = X[p * n + e] / M::sqrt_(alpha[p]);
-  }
-  __syncthreads();
-  return sweep;
 }
 
 // ---------------------------------------------------------------------------
@@ -385,7 +249,8 @@ __device__ int jacobi_rows(R* X, int rr, int n, int kk, R* VT, R* alpha,
 //      B v = sigma u; three solves with a partially pivoted LU.
 //   4. Gram-Schmidt on the u's (largest first), then V_i = Q [u_i; 0]: the
 //      right singular vectors of X.  Directions whose singular value is at or
-//      below eps * sigma_max are written as zero rows (as in jacobi_rows).
+//      below eps * sigma_max are written as zero rows, so that the kept basis
+//      stays orthonormal (the truncation stays an orthogonal projection).
 // VT (kk x n) receives the vectors in decreasing order of sigma.
 // aux: >= 3 rr + 8 scalars; inv: >= kk (13 rr) scalars; fsh: 1024
 // floats of shared memory; ush: rr scalars of shared memory.
@@ -432,12 +297,12 @@ __device__ void svd_topk_rows(R* X, int rr, int n, int kk, R* VT, R* aux, R* inv
       R xn2 = warp_sum<R>(M::acc_get(a));
       if (lane == 0) {
         R alpha = ck[k];
-        if (!(M::to(xn2) > 0.0)) {
+        if (!(M::hi(xn2) > 0)) {
           tau[k] = M::zero();
           d[k] = alpha;
         } else {
           R nrm = M::sqrt_(alpha * alpha + xn2);
-          R beta = M::to(alpha) >= 0.0 ? -nrm : nrm;
+          R beta = M::hi(alpha) >= 0 ? -nrm : nrm;
           tau[k] = (beta - alpha) / beta;
           sc[0] = M::one() / (alpha - beta);
           d[k] = beta;
@@ -445,14 +310,14 @@ __device__ void svd_topk_rows(R* X, int rr, int n, int kk, R* VT, R* aux, R* inv
         }
       }
       __syncwarp();
-      if (M::to(tau[k]) != 0.0) {
+      if (M::hi(tau[k]) != 0) {
         const R scl = sc[0];
         for (int i = k + 1 + lane; i < m; i += PEPS_WARP) ck[i] = ck[i] * scl;
       }
     }
     __syncthreads();
     const R tk = tau[k];
-    if (M::to(tk) != 0.0) reflect_columns<R>(X, n, k, k + 1, p, ck, tk);
+    if (M::hi(tk) != 0) reflect_columns<R>(X, n, k, k + 1, p, ck, tk);
     __syncthreads();
     if (k + 1 < p) {
       // row k of A over columns k+1..p-1: the entries X[c*n + k]
@@ -467,12 +332,12 @@ __device__ void svd_topk_rows(R* X, int rr, int n, int kk, R* VT, R* aux, R* inv
           R xn2 = warp_sum<R>(M::acc_get(a));
           if (lane == 0) {
             R alpha = X[(int64_t)(k + 1) * n + k];
-            if (!(M::to(xn2) > 0.0)) {
+            if (!(M::hi(xn2) > 0)) {
               sc[1] = M::zero();
               e[k] = alpha;
             } else {
               R nrm = M::sqrt_(alpha * alpha + xn2);
-              R beta = M::to(alpha) >= 0.0 ? -nrm : nrm;
+              R beta = M::hi(alpha) >= 0 ? -nrm : nrm;
               sc[1] = (beta - alpha) / beta;
               sc[2] = M::one() / (alpha - beta);
               e[k] = beta;
@@ -480,7 +345,7 @@ __device__ void svd_topk_rows(R* X, int rr, int n, int kk, R* VT, R* aux, R* inv
             }
           }
           __syncwarp();
-          const bool on = M::to(sc[1]) != 0.0;
+          const bool on = M::hi(sc[1]) != 0;
           const R scl = sc[2];
           for (int c = k + 1 + lane; c < p; c += PEPS_WARP) {
             R u = M::one();
@@ -493,7 +358,7 @@ __device__ void svd_topk_rows(R* X, int rr, int n, int kk, R* VT, R* aux, R* inv
         }
         __syncthreads();
         const R tr = sc[1];
-        if (M::to(tr) != 0.0) {
+        if (M::hi(tr) != 0) {
           for (int i = k + 1 + t; i < m; i += nt) {
             typename M::acc_t a, b;
             M::acc_init(a);
@@ -654,7 +519,7 @@ __device__ void svd_topk_rows(R* X, int rr, int n, int kk, R* VT, R* aux, R* inv
     M::acc_init(a);
     for (int i = t; i < p; i += nt) M::mac(a, uq[i], uq[i]);
     R n2 = block_sum<R>(M::acc_get(a), reinterpret_cast<R*>(red));
-    const R s = (M::to(n2) > 0.0) ? M::one() / M::sqrt_(n2) : M::zero();
+    const R s = (M::hi(n2) > 0) ? M::one() / M::sqrt_(n2) : M::zero();
     for (int i = t; i < p; i += nt) uq[i] = uq[i] * s;
     __syncthreads();
   }
@@ -667,7 +532,7 @@ __device__ void svd_topk_rows(R* X, int rr, int n, int kk, R* VT, R* aux, R* inv
     if (!(sg[q] > zero_tol)) continue;
     for (int k = p - 1; k >= 0; --k) {
       const R tk = tau[k];
-      if (M::to(tk) == 0.0) continue;
+      if (M::hi(tk) == 0) continue;
       const R* ck = X + (int64_t)k * n;
       typename M::acc_t a;
       M::acc_init(a);
