@@ -95,6 +95,10 @@ const char* peps_last_error(const peps_ctx* ctx);
 /* Bytes of device workspace a context with this shape and slot count holds
  * (host call, no allocation). */
 size_t peps_workspace_bytes(const peps_shape* shape, int32_t workspace_slots);
+/* Number of workspace slots of a context (the persistent kernels' grid):
+ * samples are processed in waves of this many.  Host call; EINVAL on a null
+ * argument. */
+int peps_slots(const peps_ctx* ctx, int32_t* slots);
 
 /* Copy the site tensors A (float64[N][2][D^4], device) into the context
  * (converting to the context's precision).  Must precede every evaluation.
@@ -204,17 +208,33 @@ int peps_amplitudes_noalloc(const peps_shape* shape, const double* A,
                             const uint8_t* spins, int64_t B, double* log_abs,
                             int8_t* sign, void* stream);
 
+/* One variational Monte Carlo step for chains chain_offset ..
+ * chain_offset+n_chains-1 in a single fused launch: each chain's current
+ * configuration chain_state[c] (uint8[n_chains][N], device, in/out) is
+ * evaluated exactly as by peps_evaluate (e_loc, log_abs, sign per chain;
+ * sum_delta, sum_delta_e, sum_e over the chains, accumulate as there), then
+ * advanced by one Metropolis sweep numbered `sweep` exactly as by
+ * peps_sample_batch (n_burn 0, n_thin 1, one sample), reusing the lower
+ * environments the evaluation built (Fig. "contraction", Steps 1-6).
+ * log_abs, sign, accepted (int64[n_chains]) may be NULL. */
+int peps_vmc_step(peps_ctx* ctx, uint64_t seed, int64_t n_chains,
+                  int64_t chain_offset, uint64_t sweep, uint8_t* chain_state,
+                  double* e_loc, double* log_abs, int8_t* sign,
+                  double* sum_delta, double* sum_delta_e, double* sum_e,
+                  int32_t accumulate, int64_t* accepted, void* stream);
+
 /* Wait for `stream` and return the device-side error state: PEPS_OK, or
  * PEPS_ENUMERIC with *flags (host, nullable) set to the PEPS_FLAG_* bits
  * seen since the last call (the bits are cleared). */
 int peps_sync_status(peps_ctx* ctx, void* stream, int32_t* flags);
 
-/* Algorithmic floating-point operation count of one sample of
- * peps_evaluate (energy + log-derivatives) under this shape, as the kernels
+/* Algorithmic floating-point operation count per chain, as the kernels
  * perform it (contractions, Householder QR, bidiagonalisation, inverse
- * iteration, back-transformation; multiply-adds count 2); host call used for
- * roofline reporting.  0 for an invalid shape. */
-double peps_flops_per_sample(const peps_shape* shape);
+ * iteration, back-transformation; a multiply-add counts 2; ratios at half
+ * filling): what = 0 one peps_evaluate sample, 1 one Metropolis sweep,
+ * 2 one peps_vmc_step (evaluation + sweep sharing the lower environments).
+ * Host call for roofline reporting; 0 for an invalid shape or `what`. */
+double peps_flops_per_sample(const peps_shape* shape, int32_t what);
 
 #ifdef __cplusplus
 }

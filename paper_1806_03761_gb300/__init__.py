@@ -36,10 +36,12 @@ def workspace_bytes(L, D, Dc, precision="fp64", slots=0, J1=1.0, J2=0.5):
     return int(_lib.load().peps_workspace_bytes(ctypes.byref(s), int(slots)))
 
 
-def flops_per_sample(L, D, Dc, precision="fp64"):
-    """Algorithmic flops of one sample of peps_evaluate (host call)."""
+def flops_per_sample(L, D, Dc, precision="fp64", what="evaluate"):
+    """Algorithmic flops per chain (host call): what = "evaluate", "sweep"
+    or "vmc" (evaluation + sweep in one peps_vmc_step)."""
     s = _shape(L, D, Dc, 1.0, 0.5, precision)
-    return float(_lib.load().peps_flops_per_sample(ctypes.byref(s)))
+    w = {"evaluate": 0, "sweep": 1, "vmc": 2}[what]
+    return float(_lib.load().peps_flops_per_sample(ctypes.byref(s), w))
 
 
 def _ptr(t):
@@ -67,6 +69,9 @@ class PepsContext:
         if rc != 0:
             raise PepsError(rc, "peps_create failed")
         self.h = h
+        n = ctypes.c_int32(0)
+        self._check(self.lib.peps_slots(self.h, ctypes.byref(n)))
+        self.slots = n.value  # samples processed concurrently (one wave)
 
     def close(self):
         if getattr(self, "h", None):
@@ -175,6 +180,25 @@ class PepsContext:
                                                int(first_sweep), _ptr(out), _ptr(state), _ptr(acc),
                                                self._stream()))
         return (out, acc) if accepted else out
+
+    def vmc_step(self, seed, state, sweep, chain_offset=0, sums=None, accumulate=False,
+                 out=None, accepted=False):
+        """Evaluate the chains' configurations and advance each by one
+        Metropolis sweep, in one launch (peps_vmc_step); `state` is updated."""
+        t = self.torch
+        assert state.dtype == t.uint8 and state.is_cuda and state.is_contiguous()
+        n = state.shape[0]
+        sums = sums or self.new_sums()
+        if out is None:
+            out = dict(e_loc=self._empty(n), log_abs=self._empty(n), sign=self._empty(n, dtype=t.int8))
+        acc = self._empty(n, dtype=t.int64) if accepted else None
+        self._check(self.lib.peps_vmc_step(
+            self.h, int(seed), n, int(chain_offset), int(sweep), _ptr(state), _ptr(out["e_loc"]),
+            _ptr(out["log_abs"]), _ptr(out["sign"]), _ptr(sums[0]), _ptr(sums[1]), _ptr(sums[2]),
+            int(bool(accumulate)), _ptr(acc), self._stream()))
+        res = dict(out)
+        res.update(sum_delta=sums[0], sum_delta_e=sums[1], sum_e=sums[2], accepted=acc)
+        return res
 
     def sync_status(self):
         f = ctypes.c_int32(0)

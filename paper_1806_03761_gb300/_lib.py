@@ -23,10 +23,10 @@ ERRNAMES = {0: "PEPS_OK", -1: "PEPS_EINVAL", -2: "PEPS_ENOMEM", -3: "PEPS_ECUDA"
             -4: "PEPS_ENUMERIC", -5: "PEPS_ETIMEOUT", -6: "PEPS_ESCRATCH"}
 
 # every entry point include/peps.h declares
-EXPORTS = ("peps_create", "peps_destroy", "peps_last_error", "peps_workspace_bytes",
+EXPORTS = ("peps_create", "peps_destroy", "peps_last_error", "peps_workspace_bytes", "peps_slots",
            "peps_set_tensors", "peps_amplitudes", "peps_local_energy", "peps_logderiv",
            "peps_evaluate", "peps_grad_step", "peps_sample_batch", "peps_sync_status",
-           "peps_flops_per_sample", "peps_amplitudes_noalloc")
+           "peps_flops_per_sample", "peps_amplitudes_noalloc", "peps_vmc_step")
 
 
 class PepsShape(ctypes.Structure):
@@ -48,6 +48,7 @@ _SIGS = {
     "peps_destroy": (I32, [P]),
     "peps_last_error": (ctypes.c_char_p, [P]),
     "peps_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(PepsShape), I32]),
+    "peps_slots": (I32, [P, ctypes.POINTER(I32)]),
     "peps_set_tensors": (I32, [P, P, P]),
     "peps_amplitudes": (I32, [P, P, I64, P, P, P]),
     "peps_local_energy": (I32, [P, P, I64, P, P, P, P, P, P]),
@@ -56,8 +57,9 @@ _SIGS = {
     "peps_grad_step": (I32, [P, P, P, P, I64, F64, U64, U64, P, P]),
     "peps_sample_batch": (I32, [P, U64, I64, I64, I32, I32, I32, U64, P, P, P, P]),
     "peps_sync_status": (I32, [P, P, ctypes.POINTER(I32)]),
-    "peps_flops_per_sample": (F64, [ctypes.POINTER(PepsShape)]),
+    "peps_flops_per_sample": (F64, [ctypes.POINTER(PepsShape), I32]),
     "peps_amplitudes_noalloc": (I32, [ctypes.POINTER(PepsShape), P, P, I64, P, P, P]),
+    "peps_vmc_step": (I32, [P, U64, I64, I64, U64, P, P, P, P, P, P, P, I32, P, P]),
 }
 
 

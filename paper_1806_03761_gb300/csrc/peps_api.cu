@@ -59,6 +59,9 @@ cudaError_t launch_eval_form(const EvalArgs<float>& a, int g, cudaStream_t s) { 
 cudaError_t launch_sample_form(const SampleArgs<double>& a, int g, cudaStream_t s) { return peps_launch_sample_f64(a, g, s); }
 cudaError_t launch_sample_form(const SampleArgs<ff>& a, int g, cudaStream_t s) { return peps_launch_sample_ff(a, g, s); }
 cudaError_t launch_sample_form(const SampleArgs<float>& a, int g, cudaStream_t s) { return peps_launch_sample_f32(a, g, s); }
+cudaError_t launch_vmc_form(const EvalArgs<double>& a, const SampleArgs<double>& b, int g, cudaStream_t s) { return peps_launch_vmc_f64(a, b, g, s); }
+cudaError_t launch_vmc_form(const EvalArgs<ff>& a, const SampleArgs<ff>& b, int g, cudaStream_t s) { return peps_launch_vmc_ff(a, b, g, s); }
+cudaError_t launch_vmc_form(const EvalArgs<float>& a, const SampleArgs<float>& b, int g, cudaStream_t s) { return peps_launch_vmc_f32(a, b, g, s); }
 
 int64_t up32(int64_t x) { return (x + 31) & ~int64_t(31); }
 
@@ -243,6 +246,42 @@ int launch_sample(peps_ctx* c, uint64_t seed, int64_t n_chains, int64_t chain_of
   return PEPS_OK;
 }
 
+template <class R>
+int launch_vmc(peps_ctx* c, uint64_t seed, int64_t n, int64_t chain_offset, uint64_t sweep,
+               uint8_t* state, double* e_loc, double* log_abs, int8_t* sign, double* sd,
+               double* sde, double* se, int accumulate, int64_t* accepted, cudaStream_t st) {
+  EvalArgs<R> a;
+  std::memset(&a, 0, sizeof(a));
+  a.P = c->plan;
+  a.steps = c->steps;
+  a.As = static_cast<const R*>(c->As);
+  a.B = n;
+  a.want_energy = 1;
+  a.want_delta = 1;
+  a.e_loc = e_loc;
+  a.log_abs = log_abs;
+  a.sign = sign;
+  a.ws = static_cast<R*>(c->ws);
+  a.wsd = c->wsd;
+  a.psum = c->psum;
+  a.flags = c->flags;
+  SampleArgs<R> s;
+  std::memset(&s, 0, sizeof(s));
+  s.k0 = (uint32_t)seed;
+  s.k1 = (uint32_t)(seed >> 32);
+  s.n_chains = n;
+  s.chain_offset = chain_offset;
+  s.first_sweep = sweep;
+  s.state = state;
+  s.accepted = accepted;
+  int grid = (int)std::min<int64_t>(c->nslots, n);
+  cudaError_t e = launch_vmc_form(a, s, grid, st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "peps_vmc_kernel launch");
+  e = peps_launch_reduce(c->psum, grid, psum_len(c->plan), sd, sde, se, accumulate, st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "peps_reduce_slots launch");
+  return PEPS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -258,6 +297,12 @@ size_t peps_workspace_bytes(const peps_shape* shape, int32_t slots) {
   return (size_t)slots * ((size_t)P.slot_elems * es + (size_t)P.slot_doubles * 8 +
                           (size_t)psum_len(P) * 8) +
          (size_t)P.N * 2 * P.D4 * es + st.size() * sizeof(PepsStep);
+}
+
+int peps_slots(const peps_ctx* c, int32_t* slots) {
+  if (!c || !slots) return PEPS_EINVAL;
+  *slots = c->nslots;
+  return PEPS_OK;
 }
 
 int peps_create(const peps_shape* shape, int32_t slots, peps_ctx** out) {
@@ -401,6 +446,33 @@ int peps_sample_batch(peps_ctx* c, uint64_t seed, int64_t n_chains, int64_t chai
                            first_sweep, spins_out, chain_state, accepted, st);
 }
 
+int peps_vmc_step(peps_ctx* c, uint64_t seed, int64_t n_chains, int64_t chain_offset,
+                  uint64_t sweep, uint8_t* chain_state, double* e_loc, double* log_abs,
+                  int8_t* sign, double* sum_delta, double* sum_delta_e, double* sum_e,
+                  int32_t accumulate, int64_t* accepted, void* stream) {
+  if (!c) return PEPS_EINVAL;
+  if (n_chains < 0) return fail(c, PEPS_EINVAL, "n_chains must be >= 0");
+  if (chain_offset < 0 || chain_offset + n_chains > (int64_t(1) << 32))
+    return fail(c, PEPS_EINVAL, "chain indices must lie in [0, 2^32)");
+  if (sweep >= (uint64_t(1) << 32)) return fail(c, PEPS_EINVAL, "sweep must be < 2^32");
+  if (accumulate != 0 && accumulate != 1) return fail(c, PEPS_EINVAL, "accumulate must be 0 or 1");
+  if (!sum_delta || !sum_delta_e || !sum_e) return fail(c, PEPS_EINVAL, "sum_delta, sum_delta_e and sum_e are required");
+  if (!c->tensors_set) return fail(c, PEPS_EINVAL, "peps_set_tensors has not been called");
+  if (n_chains == 0) return eval_common(c, nullptr, 0, 1, 1, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                        nullptr, nullptr, sum_delta, sum_delta_e, sum_e, accumulate, stream);
+  if (!chain_state || !e_loc) return fail(c, PEPS_EINVAL, "chain_state and e_loc are required");
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, PEPS_ECUDA, "cudaSetDevice failed");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (c->shape.precision == PEPS_FP64)
+    return launch_vmc<double>(c, seed, n_chains, chain_offset, sweep, chain_state, e_loc, log_abs, sign,
+                              sum_delta, sum_delta_e, sum_e, accumulate, accepted, st);
+  if (c->shape.precision == PEPS_FP32)
+    return launch_vmc<float>(c, seed, n_chains, chain_offset, sweep, chain_state, e_loc, log_abs, sign,
+                             sum_delta, sum_delta_e, sum_e, accumulate, accepted, st);
+  return launch_vmc<ff>(c, seed, n_chains, chain_offset, sweep, chain_state, e_loc, log_abs, sign,
+                        sum_delta, sum_delta_e, sum_e, accumulate, accepted, st);
+}
+
 int peps_sync_status(peps_ctx* c, void* stream, int32_t* flags) {
   if (!c) return PEPS_EINVAL;
   if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, PEPS_ECUDA, "cudaSetDevice failed");
@@ -417,49 +489,49 @@ int peps_sync_status(peps_ctx* c, void* stream, int32_t* flags) {
   return PEPS_OK;
 }
 
-double peps_flops_per_sample(const peps_shape* shape) {
+double peps_flops_per_sample(const peps_shape* shape, int32_t what) {
   std::string why;
-  if (!shape_ok(shape, &why)) return 0.0;
+  if (!shape_ok(shape, &why) || what < 0 || what > 2) return 0.0;
   PepsPlan P;
   std::vector<PepsStep> steps;
   make_plan(*shape, 1, &P, &steps);
   const int L = P.L, D = P.D;
-  double f = 0.0;
-  // environments: both directions, every step
-  for (int dir = 0; dir < 2; ++dir)
-    for (int t = 0; t < L - 1; ++t) {
-      const PepsStep& st = steps[t];
-      int rprev = 1;
-      for (int j = 0; j < L - 1; ++j) {
-        double a = st.ia[j], p = st.ip[j], b = st.ib[j];
-        double Dl = j == 0 ? 1 : D, Dr = j == L - 1 ? 1 : D;
-        double m = (double)rprev * D, n = b * Dr;
-        f += 2.0 * rprev * Dl * p * b * a;            // S1
-        f += 2.0 * rprev * D * b * Dr * Dl * p;       // X
-        double kq = std::min(m, n);
-        f += 2.0 * m * n * kq - (2.0 / 3.0) * kq * kq * kq;  // Householder R
-        rprev = st.r[j];
-      }
-      int cn = 1;
-      for (int j = L - 1; j >= 0; --j) {
-        double a = st.ia[j], p = st.ip[j], b = st.ib[j];
-        double Dl = j == 0 ? 1 : D, Dr = j == L - 1 ? 1 : D;
-        f += 2.0 * a * p * Dr * cn * b;               // S2
-        f += 2.0 * a * Dl * D * cn * p * Dr;          // Y
-        if (j == 0) break;
-        double rr = st.r[j - 1], n = (double)D * cn, A = a * Dl, kk = st.oa[j];
-        f += 2.0 * rr * n * A;                        // X_j = R Y
-        if (rr > n) f += 2.0 * rr * n * n - (2.0 / 3.0) * n * n * n;
-        double q = std::min(rr, n);
-        f += 4.0 * n * q * q - (4.0 / 3.0) * q * q * q;  // bidiagonalisation
-        f += kk * 80.0 * q;                           // inverse iteration
-        f += 2.0 * kk * kk * q;                       // Gram-Schmidt
-        f += kk * (4.0 * n * q - 2.0 * q * q);        // back-transformation
-        f += 2.0 * A * kk * n;                        // C_j
-        cn = st.oa[j];
-      }
+  // one boundary-MPS compression (absorption + truncation) of step t
+  auto compress_flops = [&](const PepsStep& st) {
+    double f = 0.0;
+    int rprev = 1;
+    for (int j = 0; j < L - 1; ++j) {
+      double a = st.ia[j], p = st.ip[j], b = st.ib[j];
+      double Dl = j == 0 ? 1 : D, Dr = j == L - 1 ? 1 : D;
+      double m = (double)rprev * D, n = b * Dr;
+      f += 2.0 * rprev * Dl * p * b * a;            // S1
+      f += 2.0 * rprev * D * b * Dr * Dl * p;       // X
+      double kq = std::min(m, n);
+      f += 2.0 * m * n * kq - (2.0 / 3.0) * kq * kq * kq;  // Householder R
+      rprev = st.r[j];
     }
-  // strips (interior estimate with the output dims of the environments)
+    int cn = 1;
+    for (int j = L - 1; j >= 0; --j) {
+      double a = st.ia[j], p = st.ip[j], b = st.ib[j];
+      double Dl = j == 0 ? 1 : D, Dr = j == L - 1 ? 1 : D;
+      f += 2.0 * a * p * Dr * cn * b;               // S2
+      f += 2.0 * a * Dl * D * cn * p * Dr;          // Y
+      if (j == 0) break;
+      double rr = st.r[j - 1], n = (double)D * cn, A = a * Dl, kk = st.oa[j];
+      f += 2.0 * rr * n * A;                        // X_j = R Y
+      if (rr > n) f += 2.0 * rr * n * n - (2.0 / 3.0) * n * n * n;
+      double q = std::min(rr, n);
+      f += 4.0 * n * q * q - (4.0 / 3.0) * q * q * q;  // bidiagonalisation
+      f += kk * 80.0 * q;                           // inverse iteration
+      f += 2.0 * kk * kk * q;                       // Gram-Schmidt
+      f += kk * (4.0 * n * q - 2.0 * q * q);        // back-transformation
+      f += 2.0 * A * kk * n;                        // C_j
+      cn = st.oa[j];
+    }
+    return f;
+  };
+  double envs = 0.0;  // one direction: L-1 compressions
+  for (int t = 0; t < L - 1; ++t) envs += compress_flops(steps[t]);
   auto ud = [&](int row, int j, int which) -> double {  // U_row dims
     if (row < 0) return 1.0;
     return which == 0 ? steps[row].oa[j] : steps[row].ob[j];
@@ -469,26 +541,36 @@ double peps_flops_per_sample(const peps_shape* shape) {
     int t = L - 1 - row;
     return which == 0 ? steps[t].oa[j] : steps[t].ob[j];
   };
+  // strips: evaluation (envs, ratios, B tensors) and sweep (right envs, left
+  // advance, num/den of the proposals), antiparallel pairs at half filling
+  double eval_strips = 0.0, sweep_strips = 0.0;
   for (int i = 0; i < L; ++i) {
     double pu = i == 0 ? 1 : D, pd = i == L - 1 ? 1 : D;
     for (int j = 0; j < L; ++j) {
       double Dl = j == 0 ? 1 : D, Dr = j == L - 1 ? 1 : D;
       double au = ud(i - 1, j, 0), bu = ud(i - 1, j, 1), ad = dd(i + 1, j, 0), bd = dd(i + 1, j, 1);
       double step1 = 2 * Dl * ad * pu * bu * au + 2 * ad * bu * Dr * pd * Dl * pu + 2 * bu * Dr * bd * ad * pd;
-      f += 2 * step1;                                        // left + right envs
-      f += 2 * Dl * ad * pu * bu * au + 2 * bu * Dr * ad * pd * bd + 2 * Dl * Dr * pu * pd * ad * bu;  // B
-      if (j + 1 < L) f += 0.5 * 2 * step1;                   // half the horizontal pairs flip (2 steps)
+      eval_strips += 2 * step1;                                        // left + right envs
+      eval_strips += 2 * Dl * ad * pu * bu * au + 2 * bu * Dr * ad * pd * bd + 2 * Dl * Dr * pu * pd * ad * bu;  // B
+      sweep_strips += 2 * step1;                                       // right env + left advance
+      if (j + 1 < L) {
+        eval_strips += 0.5 * 2 * step1;                                // horizontal ratio (2 steps)
+        sweep_strips += 0.5 * 4 * step1;                               // num + den (4 steps)
+      }
       if (i + 1 < L) {
         double pd2 = i + 1 == L - 1 ? 1 : D;
         double ad2 = dd(i + 2, j, 0), bd2 = dd(i + 2, j, 1);
         double s2 = 2 * Dl * Dl * ad2 * pu * bu * au + 2 * Dl * ad2 * bu * Dr * D * Dl * pu +
                     2 * ad2 * bu * Dr * Dr * pd2 * Dl * D + 2 * bu * Dr * Dr * bd2 * ad2 * pd2;
-        f += 2 * s2;                                         // left + right envs
-        f += 0.5 * s2 + (j + 1 < L ? 0.5 * 2 * 2 * s2 : 0);  // v, d, a ratios at half filling
+        eval_strips += 2 * s2;                                         // left + right envs
+        eval_strips += 0.5 * s2 + (j + 1 < L ? 0.5 * 2 * 2 * s2 : 0);  // v, d, a ratios
+        sweep_strips += 2 * s2 + 0.5 * 2 * s2;                         // envs + vertical num/den
       }
     }
   }
-  return f;
+  if (what == 0) return 2.0 * envs + eval_strips;
+  if (what == 1) return 2.0 * envs + sweep_strips;
+  return 3.0 * envs + eval_strips + sweep_strips;  // the fused step reuses Dn
 }
 
 }  // extern "C"

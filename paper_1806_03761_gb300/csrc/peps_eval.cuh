@@ -56,8 +56,6 @@ __device__ __forceinline__ int env2_size(const PepsPlan& P, const EnvDims& U, co
   return ed_a(U, j) * Dl * Dl * ed_a(Dn, j);
 }
 
-__device__ __forceinline__ const uint8_t* dummy_ptr() { return nullptr; }
-
 // Build the trivial environment (every site the 1x1x1 tensor [1]).
 template <class R>
 __device__ void set_trivial(const PepsPlan& P, R* env) {
@@ -218,28 +216,182 @@ __device__ double ratio_2(const PepsPlan& P, int kind, int i, int j, const uint8
   return num / den * exp(cl[j] - cl[j + ncol]);
 }
 
+// Shared memory of the per-sample kernels.
 template <class R>
-__global__ void __launch_bounds__(PEPS_NT) peps_eval_kernel(EvalArgs<R> a) {
-  __shared__ double red[PEPS_NT];
-  __shared__ __align__(16) unsigned char redR_raw[PEPS_NT * sizeof(R)];
-  __shared__ __align__(16) unsigned char wsh_raw[256 * sizeof(R)];
-  __shared__ double rot[512];
-  __shared__ int ish[264];
-  __shared__ uint8_t sp[PEPS_MAXL * PEPS_MAXL];
-  __shared__ double dnlog[PEPS_MAXL + 1];
-  __shared__ double uplog[3];
+struct BlockShared {
+  double red[PEPS_NT];
+  __align__(16) unsigned char redR_raw[PEPS_NT * sizeof(R)];
+  __align__(16) unsigned char wsh_raw[256 * sizeof(R)];
+  double rot[512];
+  int ish[264];
+  uint8_t sp[PEPS_MAXL * PEPS_MAXL];
+  double dnlog[PEPS_MAXL + 1];
+  double uplog[3];
+  int count;
+};
+
+template <class R>
+__device__ Work<R> bind_work(const PepsPlan& P, R* ws, double* wsd, BlockShared<R>& sh, int* flags) {
+  Work<R> w = make_work<R>(P, ws, wsd, blockIdx.x);
+  w.red = sh.red;
+  w.redR = reinterpret_cast<R*>(sh.redR_raw);
+  w.wsh = reinterpret_cast<R*>(sh.wsh_raw);
+  w.rot = sh.rot;
+  w.ish = sh.ish;
+  w.flags = flags;
+  return w;
+}
+
+// Evaluate sample b (spins in sh.sp): amplitude, E(S), ratios, Delta staged
+// and added to the slot partial sums ps.  dn_ready: the lower environments
+// of these spins are already in w.dn (dnlog filled).
+template <class R>
+__device__ __forceinline__ void evaluate_one(const EvalArgs<R>& a, int64_t b, BlockShared<R>& sh,
+                             const Work<R>& w, double* ps, bool dn_ready) {
   const PepsPlan& P = a.P;
   const int L = P.L, N = P.N, D4 = P.D4;
-  Work<R> w = make_work<R>(P, a.ws, a.wsd, blockIdx.x);
-  w.red = red;
-  w.redR = reinterpret_cast<R*>(redR_raw);
-  w.wsh = reinterpret_cast<R*>(wsh_raw);
-  w.rot = rot;
-  w.ish = ish;
-  w.flags = a.flags;
+  const uint8_t* sp = sh.sp;
+  double* dnlog = sh.dnlog;
+  double* uplog = sh.uplog;
   double* cl1 = w.scl;
   double* cr1 = w.scl + (L + 1);
   double* cl2 = w.scl + 2 * (L + 1);
+  const int64_t PSN = (int64_t)N * 2 * D4;
+  if (!dn_ready) build_lower<R>(P, a.steps, a.As, sp, w, dnlog);
+  // the trivial upper environment
+  set_trivial<R>(P, w.up);
+  if (threadIdx.x == 0) uplog[0] = 0.0;
+  __syncthreads();
+  // diagonal part of E(S) and the flip count
+  double e = 0.0;
+  int nflip = 0;
+  if (a.want_energy) {
+    for (int i = 0; i < L; ++i)
+      for (int j = 0; j < L; ++j) {
+        int m = i * L + j;
+        double sm = sp[m] ? -1.0 : 1.0;
+        if (j + 1 < L) { double s2 = sp[m + 1] ? -1.0 : 1.0; e += P.J1 * sm * s2 * 0.25; nflip += sp[m] != sp[m + 1]; }
+        if (i + 1 < L) { double s2 = sp[m + L] ? -1.0 : 1.0; e += P.J1 * sm * s2 * 0.25; nflip += sp[m] != sp[m + L]; }
+        if (i + 1 < L && j + 1 < L) { double s2 = sp[m + L + 1] ? -1.0 : 1.0; e += P.J2 * sm * s2 * 0.25; nflip += sp[m] != sp[m + L + 1]; }
+        if (i + 1 < L && j + 1 < L) { double s2 = sp[m + L] ? -1.0 : 1.0; double s1 = sp[m + 1] ? -1.0 : 1.0; e += P.J2 * s1 * s2 * 0.25; nflip += sp[m + 1] != sp[m + L]; }
+      }
+  }
+  double* rout = a.ratios ? a.ratios + b * P.nbonds : nullptr;
+  if (rout) {
+    for (int o = threadIdx.x; o < P.nbonds; o += blockDim.x) rout[o] = 0.0;
+    __syncthreads();
+  }
+  int ucur = 0;  // index of U_{i-1} among the three upper buffers
+  const bool full = a.want_energy || a.want_delta;
+  for (int i = 0; i < L; ++i) {
+    const R* U = w.up + (int64_t)ucur * P.env_cap;
+    EnvDims Ud = env_dims(P, a.steps, i - 1);
+    const R* Dn = w.dn + (int64_t)(i + 1) * P.env_cap;
+    EnvDims Dd = env_dims(P, a.steps, (i + 1 <= L - 1) ? (L - 2 - i) : -1);
+    strip1_build<R>(P, i, sp, a.As, U, Ud, Dn, Dd, w, cl1, cr1);
+    double wv = Arith<R>::to(w.l1[(int64_t)L * P.site_cap]);
+    double logw = log(fabs(wv)) + cl1[L] + uplog[ucur] + dnlog[i + 1];
+    if (i == 0) {
+      if (threadIdx.x == 0) {
+        if (a.log_abs) a.log_abs[b] = logw;
+        if (a.sign) a.sign[b] = (int8_t)((wv > 0.0) - (wv < 0.0));
+        if (wv == 0.0) atomicOr(a.flags, 2);
+        if (!isfinite(wv)) atomicOr(a.flags, 1);
+      }
+      if (!full) break;
+    }
+    if (a.want_energy) {
+      for (int j = 0; j + 1 < L; ++j) {
+        int m = i * L + j;
+        if (sp[m] == sp[m + 1]) continue;
+        double r = ratio_h<R>(P, i, j, sp, a.As, U, Ud, Dn, Dd, w, cl1);
+        e += P.J1 * 0.5 * r;
+        if (threadIdx.x == 0) {
+          if (rout) rout[i * (L - 1) + j] = r;
+          if (!isfinite(r)) atomicOr(a.flags, 1);
+        }
+      }
+    }
+    if (a.want_delta) {
+      for (int j = 0; j < L; ++j) {
+        int m = i * L + j;
+        Col1 k = col_dims(P, Ud, Dd, j);
+        R* Bt = w.vt;  // D^4 scalars
+        for (int o = threadIdx.x; o < D4; o += blockDim.x) Bt[o] = Arith<R>::zero();
+        __syncthreads();
+        strip1_btensor<R>(P, k, w.l1 + (int64_t)j * P.site_cap, U + j * P.site_cap,
+                          w.r1 + (int64_t)(j + 1) * P.site_cap, Dn + j * P.site_cap, Bt, w);
+        double f = exp(cl1[j] + cr1[j + 1] - cl1[L]) / wv;
+        for (int o = threadIdx.x; o < D4; o += blockDim.x)
+          w.delta[(int64_t)m * D4 + o] = Arith<R>::to(Bt[o]) * f;
+        __syncthreads();
+      }
+    }
+    if (a.want_energy && i + 1 < L) {
+      const R* Dn2 = w.dn + (int64_t)(i + 2) * P.env_cap;
+      EnvDims Dd2 = env_dims(P, a.steps, (i + 2 <= L - 1) ? (L - 3 - i) : -1);
+      strip2_build<R>(P, i, sp, a.As, U, Ud, Dn2, Dd2, w, cl2);
+      for (int j = 0; j < L; ++j) {
+        int m1 = i * L + j, m2 = m1 + L;
+        if (sp[m1] != sp[m2]) {
+          double r = ratio_2<R>(P, 0, i, j, sp, a.As, U, Ud, Dn2, Dd2, w, cl2);
+          e += P.J1 * 0.5 * r;
+          if (threadIdx.x == 0 && rout) rout[L * (L - 1) + i * L + j] = r;
+        }
+        if (j + 1 < L) {
+          if (sp[m1] != sp[m2 + 1]) {
+            double r = ratio_2<R>(P, 1, i, j, sp, a.As, U, Ud, Dn2, Dd2, w, cl2);
+            e += P.J2 * 0.5 * r;
+            if (threadIdx.x == 0 && rout) rout[2 * L * (L - 1) + i * (L - 1) + j] = r;
+          }
+          if (sp[m1 + 1] != sp[m2]) {
+            double r = ratio_2<R>(P, 2, i, j, sp, a.As, U, Ud, Dn2, Dd2, w, cl2);
+            e += P.J2 * 0.5 * r;
+            if (threadIdx.x == 0 && rout)
+              rout[2 * L * (L - 1) + (L - 1) * (L - 1) + i * (L - 1) + j] = r;
+          }
+        }
+      }
+    }
+    // U_i for the next row
+    if (i + 1 < L) {
+      int unext = (ucur == 1) ? 2 : 1;
+      double lg = compress_row<R>(P, a.steps[i], true, i, a.As, sp, U,
+                                  uplog[ucur], w.up + (int64_t)unext * P.env_cap, w);
+      __syncthreads();
+      if (threadIdx.x == 0) uplog[unext] = lg;
+      __syncthreads();
+      ucur = unext;
+    }
+  }
+  if (threadIdx.x == 0) {
+    if (a.want_energy) {
+      if (a.e_loc) a.e_loc[b] = e;
+      if (a.n_flips) a.n_flips[b] = nflip;
+      if (!isfinite(e)) atomicOr(a.flags, 1);
+    }
+  }
+  if (a.want_delta) {
+    double eb = a.want_energy ? e : a.e_in[b];
+    for (int64_t o = threadIdx.x; o < (int64_t)N * D4; o += blockDim.x) {
+      int m = (int)(o / D4), kx = (int)(o % D4);
+      double d = w.delta[o];
+      int64_t idx = ((int64_t)m * 2 + sp[m]) * D4 + kx;
+      ps[idx] += d;
+      ps[PSN + idx] += d * eb;
+      if (a.delta) a.delta[b * (int64_t)N * D4 + o] = d;
+    }
+    if (threadIdx.x == 0) ps[2 * PSN] += eb;
+  }
+  __syncthreads();
+}
+
+template <class R>
+__global__ void __launch_bounds__(PEPS_NT, 2) peps_eval_kernel(EvalArgs<R> a) {
+  __shared__ BlockShared<R> sh;
+  const PepsPlan& P = a.P;
+  const int N = P.N, D4 = P.D4;
+  Work<R> w = bind_work<R>(P, a.ws, a.wsd, sh, a.flags);
   double* ps = a.psum + (int64_t)blockIdx.x * (2 * (int64_t)N * 2 * D4 + 1);
   const int64_t PSN = (int64_t)N * 2 * D4;
   if (a.want_delta) {
@@ -247,138 +399,11 @@ __global__ void __launch_bounds__(PEPS_NT) peps_eval_kernel(EvalArgs<R> a) {
   }
   __syncthreads();
   for (int64_t b = blockIdx.x; b < a.B; b += gridDim.x) {
-    for (int m = threadIdx.x; m < N; m += blockDim.x) sp[m] = a.spins[b * N + m];
+    for (int m = threadIdx.x; m < N; m += blockDim.x) sh.sp[m] = a.spins[b * N + m];
     __syncthreads();
-    build_lower<R>(P, a.steps, a.As, sp, w, dnlog);
-    // the trivial upper environment
-    set_trivial<R>(P, w.up);
-    if (threadIdx.x == 0) uplog[0] = 0.0;
-    __syncthreads();
-    // diagonal part of E(S) and the flip count
-    double e = 0.0;
-    int nflip = 0;
-    if (a.want_energy) {
-      for (int i = 0; i < L; ++i)
-        for (int j = 0; j < L; ++j) {
-          int m = i * L + j;
-          double sm = sp[m] ? -1.0 : 1.0;
-          if (j + 1 < L) { double s2 = sp[m + 1] ? -1.0 : 1.0; e += P.J1 * sm * s2 * 0.25; nflip += sp[m] != sp[m + 1]; }
-          if (i + 1 < L) { double s2 = sp[m + L] ? -1.0 : 1.0; e += P.J1 * sm * s2 * 0.25; nflip += sp[m] != sp[m + L]; }
-          if (i + 1 < L && j + 1 < L) { double s2 = sp[m + L + 1] ? -1.0 : 1.0; e += P.J2 * sm * s2 * 0.25; nflip += sp[m] != sp[m + L + 1]; }
-          if (i + 1 < L && j + 1 < L) { double s2 = sp[m + L] ? -1.0 : 1.0; double s1 = sp[m + 1] ? -1.0 : 1.0; e += P.J2 * s1 * s2 * 0.25; nflip += sp[m + 1] != sp[m + L]; }
-        }
-    }
-    double* rout = a.ratios ? a.ratios + b * P.nbonds : nullptr;
-    if (rout) {
-      for (int o = threadIdx.x; o < P.nbonds; o += blockDim.x) rout[o] = 0.0;
-      __syncthreads();
-    }
-    int ucur = 0;  // index of U_{i-1} among the three upper buffers
-    const bool full = a.want_energy || a.want_delta;
-    for (int i = 0; i < L; ++i) {
-      const R* U = w.up + (int64_t)ucur * P.env_cap;
-      EnvDims Ud = env_dims(P, a.steps, i - 1);
-      const R* Dn = w.dn + (int64_t)(i + 1) * P.env_cap;
-      EnvDims Dd = env_dims(P, a.steps, (i + 1 <= L - 1) ? (L - 2 - i) : -1);
-      strip1_build<R>(P, i, sp, a.As, U, Ud, Dn, Dd, w, cl1, cr1);
-      double wv = Arith<R>::to(w.l1[(int64_t)L * P.site_cap]);
-      double logw = log(fabs(wv)) + cl1[L] + uplog[ucur] + dnlog[i + 1];
-      if (i == 0) {
-        if (threadIdx.x == 0) {
-          if (a.log_abs) a.log_abs[b] = logw;
-          if (a.sign) a.sign[b] = (int8_t)((wv > 0.0) - (wv < 0.0));
-          if (wv == 0.0) atomicOr(a.flags, 2);
-          if (!isfinite(wv)) atomicOr(a.flags, 1);
-        }
-        if (!full) break;
-      }
-      if (a.want_energy) {
-        for (int j = 0; j + 1 < L; ++j) {
-          int m = i * L + j;
-          if (sp[m] == sp[m + 1]) continue;
-          double r = ratio_h<R>(P, i, j, sp, a.As, U, Ud, Dn, Dd, w, cl1);
-          e += P.J1 * 0.5 * r;
-          if (threadIdx.x == 0) {
-            if (rout) rout[i * (L - 1) + j] = r;
-            if (!isfinite(r)) atomicOr(a.flags, 1);
-          }
-        }
-      }
-      if (a.want_delta) {
-        for (int j = 0; j < L; ++j) {
-          int m = i * L + j;
-          Col1 k = col_dims(P, Ud, Dd, j);
-          R* Bt = w.vt;  // D^4 scalars
-          for (int o = threadIdx.x; o < D4; o += blockDim.x) Bt[o] = Arith<R>::zero();
-          __syncthreads();
-          strip1_btensor<R>(P, k, w.l1 + (int64_t)j * P.site_cap, U + j * P.site_cap,
-                            w.r1 + (int64_t)(j + 1) * P.site_cap, Dn + j * P.site_cap, Bt, w);
-          double f = exp(cl1[j] + cr1[j + 1] - cl1[L]) / wv;
-          for (int o = threadIdx.x; o < D4; o += blockDim.x)
-            w.delta[(int64_t)m * D4 + o] = Arith<R>::to(Bt[o]) * f;
-          __syncthreads();
-        }
-      }
-      if (a.want_energy && i + 1 < L) {
-        const R* Dn2 = w.dn + (int64_t)(i + 2) * P.env_cap;
-        EnvDims Dd2 = env_dims(P, a.steps, (i + 2 <= L - 1) ? (L - 3 - i) : -1);
-        strip2_build<R>(P, i, sp, a.As, U, Ud, Dn2, Dd2, w, cl2);
-        for (int j = 0; j < L; ++j) {
-          int m1 = i * L + j, m2 = m1 + L;
-          if (sp[m1] != sp[m2]) {
-            double r = ratio_2<R>(P, 0, i, j, sp, a.As, U, Ud, Dn2, Dd2, w, cl2);
-            e += P.J1 * 0.5 * r;
-            if (threadIdx.x == 0 && rout) rout[L * (L - 1) + i * L + j] = r;
-          }
-          if (j + 1 < L) {
-            if (sp[m1] != sp[m2 + 1]) {
-              double r = ratio_2<R>(P, 1, i, j, sp, a.As, U, Ud, Dn2, Dd2, w, cl2);
-              e += P.J2 * 0.5 * r;
-              if (threadIdx.x == 0 && rout) rout[2 * L * (L - 1) + i * (L - 1) + j] = r;
-            }
-            if (sp[m1 + 1] != sp[m2]) {
-              double r = ratio_2<R>(P, 2, i, j, sp, a.As, U, Ud, Dn2, Dd2, w, cl2);
-              e += P.J2 * 0.5 * r;
-              if (threadIdx.x == 0 && rout)
-                rout[2 * L * (L - 1) + (L - 1) * (L - 1) + i * (L - 1) + j] = r;
-            }
-          }
-        }
-      }
-      // U_i for the next row
-      if (i + 1 < L) {
-        int unext = (ucur == 1) ? 2 : 1;
-        double lg = compress_row<R>(P, a.steps[i], true, i, a.As, sp, U,
-                                    uplog[ucur], w.up + (int64_t)unext * P.env_cap, w);
-        __syncthreads();
-        if (threadIdx.x == 0) uplog[unext] = lg;
-        __syncthreads();
-        ucur = unext;
-      }
-    }
-    if (threadIdx.x == 0) {
-      if (a.want_energy) {
-        if (a.e_loc) a.e_loc[b] = e;
-        if (a.n_flips) a.n_flips[b] = nflip;
-        if (!isfinite(e)) atomicOr(a.flags, 1);
-      }
-    }
-    if (a.want_delta) {
-      double eb = a.want_energy ? e : a.e_in[b];
-      for (int64_t o = threadIdx.x; o < (int64_t)N * D4; o += blockDim.x) {
-        int m = (int)(o / D4), kx = (int)(o % D4);
-        double d = w.delta[o];
-        int64_t idx = ((int64_t)m * 2 + sp[m]) * D4 + kx;
-        ps[idx] += d;
-        ps[PSN + idx] += d * eb;
-        if (a.delta) a.delta[b * (int64_t)N * D4 + o] = d;
-      }
-      if (threadIdx.x == 0) ps[2 * PSN] += eb;
-    }
-    __syncthreads();
+    evaluate_one<R>(a, b, sh, w, ps, false);
   }
 }
-
 
 template <class R>
 __global__ void peps_convert_kernel(const double* A, R* As, int64_t n, int* flags) {

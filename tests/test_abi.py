@@ -53,6 +53,8 @@ def test_workspace_and_flop_model_host_only(lib):
     assert n2 > n1 > 10 * 2 ** 20
     f = p.flops_per_sample(16, 6, 24)
     assert 1e10 < f < 5e11
+    fs, fv = p.flops_per_sample(16, 6, 24, what="sweep"), p.flops_per_sample(16, 6, 24, what="vmc")
+    assert fv < f + fs  # the fused step reuses the lower environments
     assert p.flops_per_sample(1, 6, 24) == 0.0
     assert p.workspace_bytes(1, 6, 24) == 0  # bad shape
     assert p.workspace_bytes(16, 6, 100) == 0  # Dc*D > 256

@@ -268,3 +268,32 @@ def test_zero_amplitude_is_flagged():
     rc, flags = ctx.sync_status()
     assert sg.item() == 0 and rc != 0 and flags & 2
     ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_vmc_step_equals_evaluate_then_sweep(prec):
+    """peps_vmc_step = peps_evaluate on the chain states, then one sweep of
+    peps_sample_batch (same outputs, same new states, bit for bit)."""
+    L, D, Dc = 5, 2, 4
+    A = torch.from_numpy(make_peps(L, D, seed=17)).cuda()
+    ctx = ctx_for(L, D, Dc, prec, slots=3)
+    ctx.set_tensors(A)
+    seed, n = 424242, 7
+    state0 = ctx.sample(seed, n, 2, 1, 1)  # a few sweeps from the Fisher-Yates starts
+    state = state0.clone()
+    fused = ctx.vmc_step(seed, state, sweep=9, accepted=True)
+    ref_eval = ctx.evaluate(state0.clone())
+    st = state0.clone()
+    ctx.sample(seed, n, 0, 1, 1, first_sweep=9, state=st)
+    torch.cuda.synchronize()
+    assert torch.equal(state, st)
+    for k in ("e_loc", "log_abs", "sign", "sum_delta", "sum_delta_e", "sum_e"):
+        assert torch.equal(fused[k], ref_eval[k]), k
+    # and against the oracle
+    import oracle as orc
+    ref, fin, acc = orc.sample_chains(A.cpu().numpy(), L, Dc, seed, n, 0, 1, 1,
+                                      init=state0.cpu().numpy(), first_sweep=9)
+    assert np.array_equal(state.cpu().numpy(), fin)
+    assert np.array_equal(fused["accepted"].cpu().numpy(), acc)
+    assert ctx.sync_status()[0] == 0
+    ctx.close()
