@@ -1,12 +1,17 @@
 """Benchmark of the per-sample PEPS hot path (PEPS++, arXiv:1806.03761) on GB300.
 
 One step = one variational Monte Carlo iteration over a batch of B chains:
-  1. peps_sample_batch: one Metropolis sweep per chain from its current state
-     (Fig. "contraction", Steps 1-3),
-  2. peps_evaluate: amplitudes, every J1/J2 flip ratio, E(S), Delta and the
-     gradient sums over the batch (Steps 2, 4, 5; Eqs. ess, delta, gradients),
+  1. peps_vmc_step (one fused launch per chain): the chain's configuration is
+     evaluated -- amplitude, every J1/J2 flip ratio, E(S), Delta and the
+     gradient sums (Steps 2, 4, 5; Eqs. ess, delta, gradients) -- and then
+     advanced by one Metropolis sweep that reuses the lower environments just
+     built (Steps 1-3, Fig. "contraction"),
+  2. the deterministic reduction of the per-slot sums,
   3. peps_grad_step: the sign update of the GO step.
-The metric is local-energy samples/s = B / step time (device-resident inputs).
+The metric is local-energy samples/s = B / device time of the step (chain
+states and tensors resident in HBM).  Every timed step also copies the chain
+states in from pinned host memory and the energies out, outside the device
+timing of `value` and inside that of `e2e`.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
                     [--batch B] [--workload NAME] [--impl gb300|reference]
@@ -41,12 +46,15 @@ def parse():
     p.add_argument("--steps", type=int, default=2)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "fp32"])
-    p.add_argument("--batch", type=int, default=0, help="chains per rank (0: the workload's batch)")
+    p.add_argument("--batch", type=int, default=0,
+                   help="chains per rank (0: two waves of the persistent kernel's slots)")
     p.add_argument("--workload", default=WORKLOAD, choices=sorted(CONFIGS))
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--slots", type=int, default=0)
     p.add_argument("--dt", type=float, default=1e-3)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-fp64-compare", action="store_true",
+                   help="skip the one-wave FP64 step timed beside the mixed form")
     return p.parse_args()
 
 
@@ -187,108 +195,111 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     L, D, Dc = cfg["L"], cfg["D"], cfg["Dc"]
-    B = args.batch or cfg.get("batch", cfg.get("chains", 256))
     N = L * L
     A_host = make_peps(L, D, cfg["seed"], cfg["recipe"], cfg.get("eps", 1e-2))
     A = torch.from_numpy(A_host).cuda()
     ctx = P.PepsContext(L, D, Dc, precision=args.precision, slots=args.slots)
     ctx.set_tensors(A)
+    slots = ctx.slots
+    full_batch = cfg.get("batch", cfg.get("chains", 256))
+    B = args.batch or 2 * slots
     seed = 0x5EED0000 + cfg["seed"]
     from paper_1806_03761_gb300.dist import allreduce_sums, shard
-    chain_offset, B = shard(rank, world, B)
+    chain_offset, B = shard(rank, world, B * world)
+    stream = torch.cuda.current_stream()
     # chains start from their Fisher-Yates states; every step continues them
     state = ctx.sample(seed, B, 0, 1, 1, chain_offset=chain_offset, first_sweep=1)
     state = state.view(B, N).contiguous()
-    sweep = [2]
     sums = ctx.new_sums()
     out = dict(e_loc=torch.empty(B, dtype=torch.float64, device="cuda"),
                log_abs=torch.empty(B, dtype=torch.float64, device="cuda"),
                sign=torch.empty(B, dtype=torch.int8, device="cuda"))
-    spins = torch.empty(B, N, dtype=torch.uint8, device="cuda")
-    step_no = [0]
-    stream = torch.cuda.current_stream()
-    ev_eval = []
+    counters = {"sweep": 2, "step": 0}
 
-    def vmc_step(record=False):
-        # 1. one Metropolis sweep per chain (continues from `state`)
-        P_lib = ctx.lib
-        rc = P_lib.peps_sample_batch(ctx.h, seed, B, chain_offset, 0, 1, 1, sweep[0],
-                                     P._ptr(spins), P._ptr(state), None, ctx._stream())
-        ctx._check(rc)
-        sweep[0] += 1
-        # 2. energies, ratios and Delta sums
-        if record:
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-        ctx.evaluate(spins, sums=sums, out=out)
-        if record:
-            e1.record(stream)
-            ev_eval.append((e0, e1))
+    def vmc_step(c, st, sm, o, n_total):
+        # 1+2. evaluate every chain and advance it by one sweep (one launch),
+        #      then reduce the per-slot sums
+        c.vmc_step(seed, st, counters["sweep"], chain_offset=chain_offset, sums=sm, out=o)
+        counters["sweep"] += 1
         # 3. GO update (sums all-reduced across ranks first)
-        allreduce_sums(sums, world)
-        ctx.grad_step(sums, B * world, args.dt, seed, step_no[0], A)
-        step_no[0] += 1
+        allreduce_sums(sm, world)
+        c.grad_step(sm, n_total, args.dt, seed, counters["step"], A)
+        counters["step"] += 1
 
     for _ in range(args.warmup):
-        vmc_step()
+        vmc_step(ctx, state, sums, out, B * world)
     torch.cuda.synchronize()
     barrier(world)
+
+    # pinned host buffers of the end-to-end path
+    host_state = torch.empty(B, N, dtype=torch.uint8).pin_memory()
+    host_state.copy_(state)
+    host_e = torch.empty(B, dtype=torch.float64).pin_memory()
+    host_se = torch.empty(1, dtype=torch.float64).pin_memory()
+
     clocks = ClockSampler(local)
     clocks.start()
     torch.cuda.synchronize()
     barrier(world)
-    t_start = torch.cuda.Event(enable_timing=True)
-    t_end = torch.cuda.Event(enable_timing=True)
-    step_ms = []
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    t_start, t_end = ev(), ev()
+    marks = []
     t_start.record(stream)
     for _ in range(args.steps):
-        s0 = torch.cuda.Event(enable_timing=True)
-        s1 = torch.cuda.Event(enable_timing=True)
-        s0.record(stream)
-        vmc_step(record=True)
-        s1.record(stream)
-        step_ms.append((s0, s1))
+        k0, k1, k2, k3 = ev(), ev(), ev(), ev()
+        k0.record(stream)
+        state.copy_(host_state, non_blocking=True)        # H2D: chain states
+        k1.record(stream)
+        vmc_step(ctx, state, sums, out, B * world)
+        k2.record(stream)
+        host_e.copy_(out["e_loc"], non_blocking=True)     # D2H: energies, sum E
+        host_se.copy_(sums[2], non_blocking=True)
+        host_state.copy_(state, non_blocking=True)         # and the advanced chains
+        k3.record(stream)
+        stream.synchronize()
+        marks.append((k0, k1, k2, k3))
     t_end.record(stream)
     torch.cuda.synchronize()
     barrier(world)
     clk = clocks.stop()
-    total_ms = t_start.elapsed_time(t_end)
-    total_ms = max_over_ranks(total_ms, world)
-    per_step = [a.elapsed_time(b) for a, b in step_ms]
-    eval_ms = [a.elapsed_time(b) for a, b in ev_eval]
     rc, flags = ctx.sync_status()
+    step_ms = [a.elapsed_time(b) for _, a, b, _ in marks]
+    e2e_ms = [a.elapsed_time(b) for a, _, _, b in marks]
+    dev_ms = max_over_ranks(float(np.sum(step_ms)), world) / max(args.steps, 1)
+    e2e_total = max_over_ranks(t_start.elapsed_time(t_end), world) / max(args.steps, 1)
 
-    # end to end through the public API with host buffers: pinned host chain
-    # states in, energies and the energy sum out, every step
-    e2e = None
-    if args.steps > 0:
-        host_state = torch.empty(B, N, dtype=torch.uint8).pin_memory()
-        host_state.copy_(state)
-        host_e = torch.empty(B, dtype=torch.float64).pin_memory()
-        host_se = torch.empty(1, dtype=torch.float64).pin_memory()
+    # the mixed form against the FP64 GPU path: one wave of chains, one step
+    fp64 = None
+    if args.precision == "mixed" and not args.no_fp64_compare and world == 1:
+        c64 = P.PepsContext(L, D, Dc, precision="fp64", slots=args.slots)
+        c64.set_tensors(A)
+        nb = min(B, c64.slots)
+        st64 = state[:nb].clone()
+        s64 = c64.new_sums()
+        o64 = dict(e_loc=torch.empty(nb, dtype=torch.float64, device="cuda"),
+                   log_abs=torch.empty(nb, dtype=torch.float64, device="cuda"),
+                   sign=torch.empty(nb, dtype=torch.int8, device="cuda"))
+        c64.vmc_step(seed, st64[:8].clone(), 1, sums=s64)  # warm-up launch
+        A64 = A.clone()
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            state.copy_(host_state, non_blocking=True)
-            vmc_step()
-            host_e.copy_(out["e_loc"], non_blocking=True)
-            host_se.copy_(sums[2], non_blocking=True)
-            torch.cuda.synchronize()
-            host_state.copy_(state)
-        e2e_ms = 1e3 * (time.perf_counter() - t0) / args.steps
-        e2e_ms = max_over_ranks(e2e_ms, world)
-        e2e = {"value": B * world / (e2e_ms / 1e3), "unit": "samples/s",
-               "h2d_bytes_per_step": B * N, "d2h_bytes_per_step": B * 8 + 8}
+        a64, b64 = ev(), ev()
+        a64.record(stream)
+        c64.vmc_step(seed, st64, counters["sweep"], chain_offset=chain_offset, sums=s64, out=o64)
+        c64.grad_step(s64, nb, args.dt, seed, counters["step"], A64)
+        b64.record(stream)
+        torch.cuda.synchronize()
+        t64 = a64.elapsed_time(b64)
+        fp64 = {"value": nb / (t64 / 1e3), "unit": "samples/s", "batch": nb,
+                "ms_per_step": t64, "slots": c64.slots}
+        del c64
 
     if rank != 0:
         return
-    ms = total_ms / max(args.steps, 1)
-    value = B * world / (ms / 1e3)
-    # roofline of the dominant kernel (the evaluation kernel)
-    flops = P.flops_per_sample(L, D, Dc, precision=args.precision)
-    ev = float(np.mean(eval_ms)) if eval_ms else float("nan")
-    achieved = flops * B / (ev / 1e3) / 1e12
+    value = B * world / (dev_ms / 1e3)
+    # roofline of the dominant kernel: the fused evaluation + sweep kernel
+    # (the per-slot reduction inside the same bracket is < 0.1 % of it)
+    flops = P.flops_per_sample(L, D, Dc, precision=args.precision, what="vmc")
+    achieved = flops * B / (float(np.mean(step_ms)) / 1e3) / 1e12
     sm_max = clk.get("sm_max_mhz") or 2070.0
     if args.precision == "fp64":
         peak, unit = 152 * 2 * 2 * sm_max * 1e6 / 1e12, "TFLOP/s (FP64 pipe: 2 DFMA/clk/SM)"
@@ -298,27 +309,34 @@ def main():
     else:
         peak, unit = 152 * 128 * 2 * sm_max * 1e6 / 1e12, "TFLOP/s (FP32 pipe)"
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": unit,
-            "frac": achieved / peak, "traffic": None, "kernel": "peps_eval_kernel",
-            "flops_per_sample": flops, "eval_ms": ev}
+            "frac": achieved / peak, "traffic": None, "kernel": "peps_vmc_kernel",
+            "flops_per_sample": flops, "peak_source": "unit counts x sampled max SM clock"}
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         v, cores = cpu_baseline(cfg, A_host, 1, 99)
         cpu = {"value": v, "unit": "samples/s", "cores": cores, "kind": "oracle",
                "sample": "1 chain x 1 Metropolis sweep + full evaluation (E, Delta)"}
-    lat = sorted(per_step)
+    lat = sorted(step_ms)
+    h2d, d2h = B * N, B * N + B * 8 + 8
     line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dev_ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"mixed": "ff (float-float on FP32)", "fp64": "f64", "fp32": "f32"}[args.precision],
             "data": "synthetic",
             "config": {"workload": args.workload, "L": L, "D": D, "Dc": Dc, "batch_per_gpu": B,
+                       "workload_batch": full_batch, "slots": slots,
                        "recipe": cfg["recipe"], "precision": args.precision,
-                       "step": "1 Metropolis sweep + evaluate (E, ratios, Delta sums) + GO update",
-                       "l2": "inputs and per-sample working sets exceed L2 (129 MB)"},
+                       "step": "fused evaluate (E, ratios, Delta sums) + 1 Metropolis sweep, slot "
+                               "reduction, GO update",
+                       "l2": "per-chain working sets (%d slots) exceed L2 (129 MB)" % slots},
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "local_energy_samples_per_s": B / (ev / 1e3) if eval_ms else None,
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": 4 * args.steps, "clocks": clk,
+            "latency_per": "batch (one step)",
+            "roofline": roof, "cpu_baseline": cpu,
+            "e2e": {"value": B * world / (e2e_total / 1e3), "unit": "samples/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": e2e_total, "copy_ms_per_step": float(np.mean(e2e_ms) - np.mean(step_ms))},
+            "fp64_gpu": fp64,
+            "gpu_launches": 3 * args.steps, "clocks": clk,
             "status": {"rc": rc, "flags": flags}}
     print(json.dumps(line), flush=True)
 
