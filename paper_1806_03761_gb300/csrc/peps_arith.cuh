@@ -86,6 +86,8 @@ template <> struct Arith<double> {
   PEPS_HD static void acc_init(acc_t& a) { a = 0.0; }
   PEPS_HD static void mac(acc_t& a, double x, double y) { a = fma(x, y, a); }
   PEPS_HD static double acc_get(const acc_t& a) { return a; }
+  // x - v w in one rounding
+  PEPS_HD static double sub_mul(double x, double v, double w) { return fma(-v, w, x); }
   PEPS_HD static double sqrt_(double x) { return sqrt(x); }
   PEPS_HD static double scale(double x, double s) { return x * s; }
   // relative rounding unit of the form
@@ -102,6 +104,7 @@ template <> struct Arith<float> {
   PEPS_HD static void acc_init(acc_t& a) { a = 0.0f; }
   PEPS_HD static void mac(acc_t& a, float x, float y) { a = fmaf(x, y, a); }
   PEPS_HD static float acc_get(const acc_t& a) { return a; }
+  PEPS_HD static float sub_mul(float x, float v, float w) { return fmaf(-v, w, x); }
   PEPS_HD static float sqrt_(float x) { return sqrtf(x); }
   PEPS_HD static float scale(float x, double s) { return x * (float)s; }
   PEPS_HD static double eps() { return 5.9604644775390625e-08; }  // 2^-24
@@ -131,6 +134,19 @@ template <> struct Arith<ff> {
     a.c = __fadd_rn(a.c, __fadd_rn(t.lo, e));
   }
   PEPS_HD static ff acc_get(const acc_t& a) { return ff_fast_two_sum(a.s, a.c); }
+  // x - v w: the high parts of x and of the exact product v.hi w.hi meet in
+  // one TwoSum; the product's rounding error (FMA), its cross terms and the
+  // low parts are summed in FP32 and renormalised (error a few 2^-48 of
+  // |x| + |v w|, the bound the Householder updates need).
+  PEPS_HD static ff sub_mul(ff x, ff v, ff w) {
+    float p = __fmul_rn(v.hi, w.hi);
+    float e = fmaf(v.hi, w.hi, -p);
+    e = fmaf(v.hi, w.lo, e);
+    e = fmaf(v.lo, w.hi, e);
+    ff t = ff_two_sum(x.hi, -p);
+    float l = __fadd_rn(__fsub_rn(x.lo, e), t.lo);
+    return ff_two_sum(t.hi, l);  // t.hi may have cancelled below |l|
+  }
   PEPS_HD static ff sqrt_(ff x) { return ff_sqrt(x); }
   PEPS_HD static ff scale(ff x, double s) { return x * ff_from_double(s); }
   PEPS_HD static double eps() { return 3.552713678800501e-15; }  // 2^-48

@@ -177,24 +177,24 @@ __device__ __forceinline__ void reflect_columns(R* X, int m, int k, int c0, int 
     }
     for (int i = k + 1 + lane; i < m; i += PEPS_WARP) {
       const R v = xk[i];
-      xa[i] = xa[i] - v * wa;
-      if (two) xb[i] = xb[i] - v * wb;
+      xa[i] = Arith<R>::sub_mul(xa[i], v, wa);
+      if (two) xb[i] = Arith<R>::sub_mul(xb[i], v, wb);
     }
   }
 }
 
 // ---------------------------------------------------------------------------
 // Householder QR, R factor only (LAPACK-style reflectors H = I - tau v v^T,
-// v_k = 1).  X is m x n COLUMN-major (X[c*m + i]), overwritten.  The first
-// min(m,n) rows of R are written row-major to Rout (ld n), zeros below the
-// diagonal.  Warp 0 forms each reflector; then it is applied to the columns
-// on its right, two columns per warp.  (A blocked compact-WY variant was
-// measured: about 20 % faster in isolation in float-float, slower in FP64,
-// and its accumulator arrays made the fused kernel spill registers.)
-// sh: >= 2 scalars of shared memory.
+// v_k = 1).  X is m x n COLUMN-major (X[c*m + i]), overwritten: R on and
+// above the diagonal, the reflector tails below.  The first min(m,n) rows of
+// R are written row-major to Rout (ld n), zeros below the diagonal.
+//
+// Unblocked form: warp 0 forms each reflector, which is then applied to the
+// columns on its right, two columns per warp (every trailing column is read
+// twice and written once per reflector).  sh: >= 2 scalars of shared memory.
 // ---------------------------------------------------------------------------
 template <class R>
-__device__ void householder_r(R* X, int m, int n, R* Rout, R* sh) {
+__device__ void householder_r_unblocked(R* X, int m, int n, R* Rout, R* sh) {
   typedef Arith<R> M;
   const int t = threadIdx.x, lane = t % PEPS_WARP, wid = t / PEPS_WARP;
   const int kmax = m < n ? m : n;
@@ -225,6 +225,156 @@ __device__ void householder_r(R* X, int m, int n, R* Rout, R* sh) {
     __syncthreads();
     const R tau = sh[0];
     if (M::hi(tau) != 0) reflect_columns<R>(X, m, k, k + 1, n, xk, tau);
+    __syncthreads();
+  }
+  for (int o = t; o < kmax * n; o += blockDim.x) {
+    int i = o / n, c = o % n;
+    Rout[o] = (c >= i) ? X[(int64_t)c * m + i] : M::zero();
+  }
+  __syncthreads();
+}
+
+// Panel width and row capacity of the blocked form.
+#ifndef PEPS_QR_NB
+#define PEPS_QR_NB 4
+#endif
+#define PEPS_QR_ROWS 896
+
+// Apply the panel's reflectors (explicit vectors v_s, zero above row s and
+// one at row s, in vsh with stride PEPS_QR_ROWS; taus in tau[]) to the
+// trailing columns c0..n-1 of X, rows k0..k0+mr-1.  One warp per column: the
+// column is held in registers (CAP rows per lane), every reflector is applied
+// to it in order, and it is written back once.
+template <class R, int CAP>
+__device__ __forceinline__ void qr_trailing(R* X, int m, int n, int k0, int mr, int c0, int nb,
+                                            const R* vsh, const R* tau) {
+  typedef Arith<R> M;
+  const int lane = threadIdx.x % PEPS_WARP, wid = threadIdx.x / PEPS_WARP;
+  const int nw = (blockDim.x + PEPS_WARP - 1) / PEPS_WARP;
+  for (int c = c0 + wid; c < n; c += nw) {
+    R* x = X + (int64_t)c * m + k0;
+    R xr[CAP];
+#pragma unroll
+    for (int q = 0; q < CAP; ++q) {
+      const int i = lane + q * PEPS_WARP;
+      xr[q] = i < mr ? x[i] : M::zero();
+    }
+    for (int s = 0; s < nb; ++s) {
+      const R ts = tau[s];
+      if (M::hi(ts) == 0) continue;
+      const R* v = vsh + s * PEPS_QR_ROWS;
+      typename M::acc_t a0, a1;
+      M::acc_init(a0);
+      M::acc_init(a1);
+#pragma unroll
+      for (int q = 0; q < CAP; q += 2) {
+        const int i = lane + q * PEPS_WARP;
+        if (i < mr) M::mac(a0, v[i], xr[q]);
+        if (q + 1 < CAP && i + PEPS_WARP < mr) M::mac(a1, v[i + PEPS_WARP], xr[q + 1]);
+      }
+      const R wv = ts * warp_sum<R>(M::acc_get(a0) + M::acc_get(a1));
+#pragma unroll
+      for (int q = 0; q < CAP; ++q) {
+        const int i = lane + q * PEPS_WARP;
+        if (i < mr) xr[q] = M::sub_mul(xr[q], v[i], wv);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < CAP; ++q) {
+      const int i = lane + q * PEPS_WARP;
+      if (i < mr) x[i] = xr[q];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Blocked form of householder_r (the same reflectors, applied in the same
+// order to every column): panels of PEPS_QR_NB columns are factored in
+// shared memory, then applied to the trailing columns held in registers, so
+// that a trailing column is read and written once per panel instead of three
+// times per reflector.  vsh: PEPS_QR_NB * PEPS_QR_ROWS scalars of shared
+// memory; sh: >= 2 * PEPS_QR_NB scalars.  Falls back to the unblocked form
+// when m > PEPS_QR_ROWS or vsh is null.
+// ---------------------------------------------------------------------------
+template <class R>
+__device__ __noinline__ void householder_r(R* X, int m, int n, R* Rout, R* sh, R* vsh) {
+  typedef Arith<R> M;
+  if (vsh == nullptr || m > PEPS_QR_ROWS) {
+    householder_r_unblocked<R>(X, m, n, Rout, sh);
+    return;
+  }
+  const int t = threadIdx.x, lane = t % PEPS_WARP, wid = t / PEPS_WARP;
+  const int nw = (blockDim.x + PEPS_WARP - 1) / PEPS_WARP;
+  const int kmax = m < n ? m : n;
+  R* tau = sh;
+  for (int k0 = 0; k0 < kmax; k0 += PEPS_QR_NB) {
+    const int nb = kmax - k0 < PEPS_QR_NB ? kmax - k0 : PEPS_QR_NB;
+    const int mr = m - k0;
+    // 1. the panel (rows k0.., columns k0..k0+nb-1) into shared memory
+    for (int o = t; o < nb * mr; o += blockDim.x) {
+      const int r = o / mr, i = o - r * mr;
+      vsh[r * PEPS_QR_ROWS + i] = X[(int64_t)(k0 + r) * m + k0 + i];
+    }
+    __syncthreads();
+    // 2. unblocked factorisation of the panel (its diagonal is at row s of
+    //    column s)
+    for (int s = 0; s < nb; ++s) {
+      R* v = vsh + s * PEPS_QR_ROWS;
+      if (wid == 0) {
+        typename M::acc_t a;
+        M::acc_init(a);
+        for (int i = s + 1 + lane; i < mr; i += PEPS_WARP) M::mac(a, v[i], v[i]);
+        R xn2 = warp_sum<R>(M::acc_get(a));
+        if (lane == 0) {
+          R alpha = v[s];
+          if (!(M::hi(xn2) > 0)) {
+            tau[s] = M::zero();
+            tau[PEPS_QR_NB] = M::zero();
+          } else {
+            R nrm = M::sqrt_(alpha * alpha + xn2);
+            R beta = M::hi(alpha) >= 0 ? -nrm : nrm;
+            tau[s] = (beta - alpha) / beta;
+            tau[PEPS_QR_NB] = M::one() / (alpha - beta);
+            v[s] = beta;
+          }
+        }
+        __syncwarp();
+        const R scl = tau[PEPS_QR_NB];
+        if (M::hi(tau[s]) != 0)
+          for (int i = s + 1 + lane; i < mr; i += PEPS_WARP) v[i] = v[i] * scl;
+      }
+      __syncthreads();
+      const R ts = tau[s];
+      if (M::hi(ts) != 0) {
+        for (int c = s + 1 + wid; c < nb; c += nw) {
+          R* x = vsh + c * PEPS_QR_ROWS;
+          typename M::acc_t a;
+          M::acc_init(a);
+          if (lane == 0) M::mac(a, M::one(), x[s]);
+          for (int i = s + 1 + lane; i < mr; i += PEPS_WARP) M::mac(a, v[i], x[i]);
+          const R wv = ts * warp_sum<R>(M::acc_get(a));
+          if (lane == 0) x[s] = x[s] - wv;
+          for (int i = s + 1 + lane; i < mr; i += PEPS_WARP) x[i] = M::sub_mul(x[i], v[i], wv);
+        }
+      }
+      __syncthreads();
+    }
+    // 3. R entries and reflector tails back to X; explicit reflectors
+    //    (zero above the diagonal, one on it) left in shared memory
+    for (int o = t; o < nb * mr; o += blockDim.x) {
+      const int r = o / mr, i = o - r * mr;
+      R* p = vsh + r * PEPS_QR_ROWS + i;
+      X[(int64_t)(k0 + r) * m + k0 + i] = *p;
+      if (i <= r) *p = (i == r) ? M::one() : M::zero();
+    }
+    __syncthreads();
+    // 4. the trailing columns
+    if (k0 + nb < n) {
+      if (mr <= 8 * PEPS_WARP)
+        qr_trailing<R, (8 * PEPS_WARP + PEPS_WARP - 1) / PEPS_WARP>(X, m, n, k0, mr, k0 + nb, nb, vsh, tau);
+      else
+        qr_trailing<R, (PEPS_QR_ROWS + PEPS_WARP - 1) / PEPS_WARP>(X, m, n, k0, mr, k0 + nb, nb, vsh, tau);
+    }
     __syncthreads();
   }
   for (int o = t; o < kmax * n; o += blockDim.x) {

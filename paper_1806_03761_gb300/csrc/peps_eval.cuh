@@ -11,6 +11,7 @@
 template <class R>
 __device__ Work<R> make_work(const PepsPlan& P, R* ws, double* wsd, int slot) {
   Work<R> w;
+  w.qrv = nullptr;  // the shared-memory pointers are bound by the kernel
   R* base = ws + (int64_t)slot * P.slot_elems;
   double* bd = wsd + (int64_t)slot * P.slot_doubles;
   w.dn = base + P.off_dn;
@@ -222,6 +223,7 @@ struct BlockShared {
   double red[PEPS_NT];
   __align__(16) unsigned char redR_raw[PEPS_NT * sizeof(R)];
   __align__(16) unsigned char wsh_raw[256 * sizeof(R)];
+  __align__(16) unsigned char qrv_raw[PEPS_QR_NB * PEPS_QR_ROWS * sizeof(R)];
   double rot[512];
   int ish[264];
   uint8_t sp[PEPS_MAXL * PEPS_MAXL];
@@ -236,6 +238,7 @@ __device__ Work<R> bind_work(const PepsPlan& P, R* ws, double* wsd, BlockShared<
   w.red = sh.red;
   w.redR = reinterpret_cast<R*>(sh.redR_raw);
   w.wsh = reinterpret_cast<R*>(sh.wsh_raw);
+  w.qrv = reinterpret_cast<R*>(sh.qrv_raw);
   w.rot = sh.rot;
   w.ish = sh.ish;
   w.flags = flags;

@@ -38,6 +38,7 @@ struct Work {
   double* red;
   R* redR;
   R* wsh;
+  R* qrv;  // PEPS_QR_NB * PEPS_QR_ROWS: the blocked QR's panel (null: unblocked)
   double* rot;
   int* ish;
   int* flags;
@@ -119,7 +120,7 @@ __device__ double compress_row(const PepsPlan& P, const PepsStep& st, bool above
     c.k1 = Dl; c.ka1 = p * b; c.kb1 = D3;
     c.k2 = p; c.ka2 = b; c.kb2 = sP;
     contract<R>(c, w.b0, T, w.b1);
-    householder_r<R>(w.b1, mrow, Bj, w.rst + (int64_t)(j + 1) * MC, w.wsh);
+    householder_r<R>(w.b1, mrow, Bj, w.rst + (int64_t)(j + 1) * MC, w.wsh, w.qrv);
     rprev = st.r[j];
     // only the row space of R_j matters: keep it at unit scale so that the
     // float-float form stays inside the FP32 exponent range
@@ -178,7 +179,7 @@ __device__ double compress_row(const PepsPlan& P, const PepsStep& st, bool above
     normalize_pow2<R>(w.xj, rr * n, w.red);
     float* fsh = reinterpret_cast<float*>(w.rot);
     if (rr > n) {
-      householder_r<R>(w.xj, rr, n, w.b2, w.wsh);
+      householder_r<R>(w.xj, rr, n, w.b2, w.wsh, w.qrv);
       svd_topk_rows<R>(w.b2, n, n, kk, V, w.alpha, w.inv, fsh, w.wsh, w.red);
     } else {
       svd_topk_rows<R>(w.xj, rr, n, kk, V, w.alpha, w.inv, fsh, w.wsh, w.red);

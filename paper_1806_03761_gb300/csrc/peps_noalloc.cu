@@ -46,6 +46,7 @@ __global__ void __launch_bounds__(PEPS_NT, 2) peps_amp_noalloc_kernel(EvalArgs<d
   __shared__ double red[PEPS_NT];
   __shared__ __align__(16) unsigned char redR_raw[PEPS_NT * sizeof(double)];
   __shared__ __align__(16) unsigned char wsh_raw[256 * sizeof(double)];
+  __shared__ __align__(16) unsigned char qrv_raw[PEPS_QR_NB * PEPS_QR_ROWS * sizeof(double)];
   __shared__ double rot[512];
   __shared__ int ish[264];
   __shared__ uint8_t sp[PEPS_MAXL * PEPS_MAXL];
@@ -56,6 +57,7 @@ __global__ void __launch_bounds__(PEPS_NT, 2) peps_amp_noalloc_kernel(EvalArgs<d
   w.red = red;
   w.redR = reinterpret_cast<double*>(redR_raw);
   w.wsh = reinterpret_cast<double*>(wsh_raw);
+  w.qrv = reinterpret_cast<double*>(qrv_raw);
   w.rot = rot;
   w.ish = ish;
   w.flags = a.flags;
