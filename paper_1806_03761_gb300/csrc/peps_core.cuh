@@ -85,12 +85,74 @@ __device__ __forceinline__ Ctr ctr_init() {
 
 // The operands are scratch rewritten within the same kernel, so they are
 // read through the coherent path (no __restrict__ / read-only cache).
+//
+// Register blocking: when the output has a digit carried only by A (dA) and
+// one carried only by B (dB), each thread computes the 2 x 2 outputs
+// (2x, 2x+1) x (2y, 2y+1) over those digits, so that every loaded element of
+// either operand feeds two multiply-adds.  Otherwise each thread computes two
+// outputs adjacent in the fastest digit (shared loads where an operand does
+// not carry it).
 template <class R>
 __device__ void contract(const Ctr& d, const R* A, const R* B, R* C) {
   typedef Arith<R> M;
-  // each thread computes two outputs adjacent in the fastest digit (two
-  // independent accumulations, shared loads where an operand does not carry
-  // that digit)
+  int dA = -1, dB = -1;
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    if (d.e[i] > 1 && d.sa[i] != 0 && d.sb[i] == 0) dA = i;
+    if (d.e[i] > 1 && d.sb[i] != 0 && d.sa[i] == 0) dB = i;
+  }
+  if (dA >= 0 && dB >= 0) {
+    int eb[5];
+    int tot = 1;
+    int sA = 0, sB = 0, cA = 0, cB = 0, nA = 1, nB = 1;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      const bool bl = (i == dA) || (i == dB);
+      eb[i] = bl ? (d.e[i] + 1) >> 1 : d.e[i];
+      tot *= eb[i];
+      if (i == dA) { sA = d.sa[i]; cA = d.sc[i]; nA = d.e[i]; }
+      if (i == dB) { sB = d.sb[i]; cB = d.sc[i]; nB = d.e[i]; }
+    }
+    for (int o = threadIdx.x; o < tot; o += blockDim.x) {
+      int t = o;
+      int oa = 0, ob = 0, oc = 0, xA = 0, xB = 0;
+#pragma unroll
+      for (int i = 4; i >= 0; --i) {
+        int q = t % eb[i];
+        t /= eb[i];
+        if (i == dA) { q *= 2; xA = q; }
+        if (i == dB) { q *= 2; xB = q; }
+        oa += q * d.sa[i];
+        ob += q * d.sb[i];
+        oc += q * d.sc[i];
+      }
+      const bool vA = xA + 1 < nA, vB = xB + 1 < nB;
+      const int da = vA ? sA : 0, db = vB ? sB : 0;
+      typename M::acc_t c00, c01, c10, c11;
+      M::acc_init(c00);
+      M::acc_init(c01);
+      M::acc_init(c10);
+      M::acc_init(c11);
+      for (int k1 = 0; k1 < d.k1; ++k1) {
+        const R* pa = A + oa + k1 * d.ka1;
+        const R* pb = B + ob + k1 * d.kb1;
+        for (int k2 = 0; k2 < d.k2; ++k2) {
+          const R a0 = pa[k2 * d.ka2], a1 = pa[k2 * d.ka2 + da];
+          const R b0 = pb[k2 * d.kb2], b1 = pb[k2 * d.kb2 + db];
+          M::mac(c00, a0, b0);
+          M::mac(c01, a0, b1);
+          M::mac(c10, a1, b0);
+          M::mac(c11, a1, b1);
+        }
+      }
+      C[oc] = M::acc_get(c00);
+      if (vB) C[oc + cB] = M::acc_get(c01);
+      if (vA) C[oc + cA] = M::acc_get(c10);
+      if (vA && vB) C[oc + cA + cB] = M::acc_get(c11);
+    }
+    __syncthreads();
+    return;
+  }
   const int e4 = d.e[4];
   const int h4 = (e4 + 1) >> 1;
   const int tot = d.e[0] * d.e[1] * d.e[2] * d.e[3] * h4;
@@ -385,6 +447,227 @@ __device__ __noinline__ void householder_r(R* X, int m, int n, R* Rout, R* sh, R
 }
 
 // ---------------------------------------------------------------------------
+// Blocked Golub-Kahan bidiagonalisation of A (m x p column-major, ld m,
+// m >= p): A = Q B P^T with B upper bidiagonal (d, e).  The left reflectors
+// (tau, tails below the diagonal of A's columns, v_k = 1) are kept for the
+// back-transformation; the right ones are dropped.  Panels of nb steps: within
+// a panel the trailing matrix is left as stored and the reflectors' effect is
+// carried by four thin matrices (the panel's left vectors V, right vectors U
+// and the products W = tau_p A' u, Y = tau_q A'^T v), so that A' = A - V Y^T
+// - W U^T; each step reads the trailing matrix twice (A^T v and A u), and the
+// panel's rank-2nb update is written once at its end (the blocking of Dongarra,
+// Sorensen and Hammarling, 1989).
+// pan: (2m + 2p) nb scalars of shared memory; sc: >= 2 nb + 8 scalars of
+// shared memory.
+// ---------------------------------------------------------------------------
+template <class R>
+__device__ void bidiag_blocked(R* A, int m, int p, int nb, R* d, R* e, R* tau, R* pan, R* sc) {
+  typedef Arith<R> M;
+  const int t = threadIdx.x, nt = blockDim.x;
+  const int lane = t % PEPS_WARP, wid = t / PEPS_WARP, nw = (nt + PEPS_WARP - 1) / PEPS_WARP;
+  R* Vp = pan;               // Vp[l*m + i]
+  R* Wp = Vp + nb * m;       // Wp[l*m + i]
+  R* Up = Wp + nb * m;       // Up[l*p + c]
+  R* Yp = Up + nb * p;       // Yp[l*p + c]
+  R* cf = sc + 8;            // 2 nb + 1 correction coefficients
+  for (int i0 = 0; i0 < p; i0 += nb) {
+    const int nbp = p - i0 < nb ? p - i0 : nb;
+    for (int j = 0; j < nbp; ++j) {
+      const int k = i0 + j;
+      R* v = Vp + j * m;
+      R* u = Up + j * p;
+      // (a) column k of the current matrix, rows k..m-1, into Vp[:, j]
+      for (int i = t; i < m; i += nt) {
+        R x = M::zero();
+        if (i >= k) {
+          typename M::acc_t a;
+          M::acc_init(a);
+          M::mac(a, M::one(), A[(int64_t)k * m + i]);
+          for (int l = 0; l < j; ++l) {
+            M::mac(a, Vp[l * m + i], -Yp[l * p + k]);
+            M::mac(a, Wp[l * m + i], -Up[l * p + k]);
+          }
+          x = M::acc_get(a);
+        }
+        v[i] = x;
+      }
+      __syncthreads();
+      // (b) the left reflector: d_k, tau_k, v (v_k = 1), tail kept in A
+      if (wid == 0) {
+        typename M::acc_t a;
+        M::acc_init(a);
+        for (int i = k + 1 + lane; i < m; i += PEPS_WARP) M::mac(a, v[i], v[i]);
+        const R xn2 = warp_sum<R>(M::acc_get(a));
+        if (lane == 0) {
+          const R alpha = v[k];
+          if (!(M::hi(xn2) > 0)) {
+            tau[k] = M::zero();
+            d[k] = alpha;
+            sc[0] = M::zero();
+          } else {
+            const R nrm = M::sqrt_(alpha * alpha + xn2);
+            const R beta = M::hi(alpha) >= 0 ? -nrm : nrm;
+            tau[k] = (beta - alpha) / beta;
+            sc[0] = M::one() / (alpha - beta);
+            d[k] = beta;
+          }
+        }
+        __syncwarp();
+        const R tq = tau[k], scl = sc[0];
+        for (int i = k + 1 + lane; i < m; i += PEPS_WARP) {
+          const R x = M::hi(tq) != 0 ? v[i] * scl : M::zero();
+          v[i] = x;
+          A[(int64_t)k * m + i] = x;
+        }
+        if (lane == 0) v[k] = M::one();
+      }
+      __syncthreads();
+      const R tq = tau[k];
+      const int nc = p - k - 1;  // trailing columns k+1..p-1
+      if (nc <= 0) break;        // the last column: no row reflector
+      // (c) Y[:, j] = tau_q (A'^T v) over columns k+1..p-1, with
+      //     A'^T v = A^T v - Y (V^T v) - U (W^T v)
+      if (M::hi(tq) != 0) {
+        for (int q = wid; q < nc + 2 * j; q += nw) {
+          typename M::acc_t a;
+          M::acc_init(a);
+          if (q < nc) {
+            const R* col = A + (int64_t)(k + 1 + q) * m;
+            for (int i = k + lane; i < m; i += PEPS_WARP) M::mac(a, col[i], v[i]);
+          } else {
+            const int l = q - nc;  // l < j: V^T v, else W^T v
+            const R* x = l < j ? Vp + l * m : Wp + (l - j) * m;
+            for (int i = k + lane; i < m; i += PEPS_WARP) M::mac(a, x[i], v[i]);
+          }
+          const R r = warp_sum<R>(M::acc_get(a));
+          if (lane == 0) {
+            if (q < nc) Yp[j * p + k + 1 + q] = r;
+            else cf[q - nc] = r;
+          }
+        }
+      }
+      __syncthreads();
+      for (int c = t; c < p; c += nt) {
+        R y = M::zero();
+        if (c > k && M::hi(tq) != 0) {
+          typename M::acc_t a;
+          M::acc_init(a);
+          M::mac(a, M::one(), Yp[j * p + c]);
+          for (int l = 0; l < j; ++l) {
+            M::mac(a, Yp[l * p + c], -cf[l]);
+            M::mac(a, Up[l * p + c], -cf[j + l]);
+          }
+          y = tq * M::acc_get(a);
+        }
+        Yp[j * p + c] = y;
+      }
+      __syncthreads();
+      // (d) row k of the current matrix after the left reflector, columns
+      //     k+1..p-1, into Up[:, j]
+      for (int c = t; c < p; c += nt) {
+        R x = M::zero();
+        if (c > k) {
+          typename M::acc_t a;
+          M::acc_init(a);
+          M::mac(a, M::one(), A[(int64_t)c * m + k]);
+          for (int l = 0; l <= j; ++l) M::mac(a, Vp[l * m + k], -Yp[l * p + c]);
+          for (int l = 0; l < j; ++l) M::mac(a, Wp[l * m + k], -Up[l * p + c]);
+          x = M::acc_get(a);
+        }
+        u[c] = x;
+      }
+      __syncthreads();
+      // (e) the right reflector on u[k+1..p-1]: e_k, tau_p, u (u_{k+1} = 1)
+      if (wid == 0) {
+        typename M::acc_t a;
+        M::acc_init(a);
+        for (int c = k + 2 + lane; c < p; c += PEPS_WARP) M::mac(a, u[c], u[c]);
+        const R xn2 = warp_sum<R>(M::acc_get(a));
+        if (lane == 0) {
+          const R alpha = u[k + 1];
+          if (!(M::hi(xn2) > 0)) {
+            sc[1] = M::zero();
+            e[k] = alpha;
+            sc[2] = M::zero();
+          } else {
+            const R nrm = M::sqrt_(alpha * alpha + xn2);
+            const R beta = M::hi(alpha) >= 0 ? -nrm : nrm;
+            sc[1] = (beta - alpha) / beta;
+            sc[2] = M::one() / (alpha - beta);
+            e[k] = beta;
+          }
+        }
+        __syncwarp();
+        const R tp = sc[1], scl = sc[2];
+        for (int c = k + 2 + lane; c < p; c += PEPS_WARP) u[c] = M::hi(tp) != 0 ? u[c] * scl : M::zero();
+        if (lane == 0) u[k + 1] = M::one();
+      }
+      __syncthreads();
+      // (f) W[:, j] = tau_p (A' u) over rows k+1..m-1, with
+      //     A' u = A u - V (Y^T u) - W (U^T u)   (Y, V including column j)
+      const R tp = sc[1];
+      if (M::hi(tp) != 0) {
+        // coefficients: Y^T u (j + 1 of them), U^T u (j of them)
+        for (int q = wid; q < 2 * j + 1; q += nw) {
+          const R* x = q <= j ? Yp + q * p : Up + (q - j - 1) * p;
+          typename M::acc_t a;
+          M::acc_init(a);
+          for (int c = k + 1 + lane; c < p; c += PEPS_WARP) M::mac(a, x[c], u[c]);
+          const R r = warp_sum<R>(M::acc_get(a));
+          if (lane == 0) cf[q] = r;
+        }
+        // A u: one warp per 32-row chunk, every column
+        for (int ch = wid; ch * PEPS_WARP + k + 1 < m; ch += nw) {
+          const int i = k + 1 + ch * PEPS_WARP + lane;
+          typename M::acc_t a0, a1;
+          M::acc_init(a0);
+          M::acc_init(a1);
+          if (i < m) {
+            int c = k + 1;
+            for (; c + 1 < p; c += 2) {
+              M::mac(a0, A[(int64_t)c * m + i], u[c]);
+              M::mac(a1, A[(int64_t)(c + 1) * m + i], u[c + 1]);
+            }
+            if (c < p) M::mac(a0, A[(int64_t)c * m + i], u[c]);
+            Wp[j * m + i] = M::acc_get(a0) + M::acc_get(a1);
+          }
+        }
+      }
+      __syncthreads();
+      for (int i = t; i < m; i += nt) {
+        R x = M::zero();
+        if (i > k && M::hi(tp) != 0) {
+          typename M::acc_t a;
+          M::acc_init(a);
+          M::mac(a, M::one(), Wp[j * m + i]);
+          for (int l = 0; l <= j; ++l) M::mac(a, Vp[l * m + i], -cf[l]);
+          for (int l = 0; l < j; ++l) M::mac(a, Wp[l * m + i], -cf[j + 1 + l]);
+          x = tp * M::acc_get(a);
+        }
+        Wp[j * m + i] = x;
+      }
+      __syncthreads();
+    }
+    // the panel's update of the trailing matrix (rows, columns >= i0 + nbp)
+    const int k1 = i0 + nbp;
+    for (int c = k1 + wid; c < p; c += nw) {
+      R* col = A + (int64_t)c * m;
+      for (int i = k1 + lane; i < m; i += PEPS_WARP) {
+        typename M::acc_t a;
+        M::acc_init(a);
+        M::mac(a, M::one(), col[i]);
+        for (int l = 0; l < nbp; ++l) {
+          M::mac(a, Vp[l * m + i], -Yp[l * p + c]);
+          M::mac(a, Wp[l * m + i], -Up[l * p + c]);
+        }
+        col[i] = M::acc_get(a);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Top-kk right singular vectors of X (rr x n row-major, 1 <= rr <= n) by
 // Golub-Kahan bidiagonalisation, bisection and inverse iteration:
 //   1. A = X^T (n x rr, column c = row c of X) = Q B P^T with B upper
@@ -427,8 +710,8 @@ __device__ __forceinline__ int bidiag_count(const float* d, const float* e, int 
 }
 
 template <class R>
-__device__ void svd_topk_rows(R* X, int rr, int n, int kk, R* VT, R* aux, R* inv,
-                              float* fsh, R* ush, double* red) {
+__device__ __noinline__ void svd_topk_rows(R* X, int rr, int n, int kk, R* VT, R* aux, R* inv,
+                              float* fsh, R* ush, double* red, R* vsh) {
   typedef Arith<R> M;
   const int t = threadIdx.x, nt = blockDim.x;
   const int lane = t % PEPS_WARP, wid = t / PEPS_WARP, nw = (nt + PEPS_WARP - 1) / PEPS_WARP;
@@ -438,6 +721,10 @@ __device__ void svd_topk_rows(R* X, int rr, int n, int kk, R* VT, R* aux, R* inv
   R* tau = aux + 2 * p;
   R* sc = aux + 3 * p;  // scalars
   // ---- 1. bidiagonalisation ---------------------------------------------
+  const int nbb = vsh ? (PEPS_QR_NB * PEPS_QR_ROWS) / (2 * m + 2 * p) : 0;
+  if (nbb >= 2) {
+    bidiag_blocked<R>(X, m, p, nbb < 8 ? nbb : 8, d, e, tau, vsh, ush);
+  } else
   for (int k = 0; k < p; ++k) {
     R* ck = X + (int64_t)k * n;
     if (wid == 0) {

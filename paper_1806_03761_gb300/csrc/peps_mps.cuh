@@ -180,9 +180,9 @@ __device__ double compress_row(const PepsPlan& P, const PepsStep& st, bool above
     float* fsh = reinterpret_cast<float*>(w.rot);
     if (rr > n) {
       householder_r<R>(w.xj, rr, n, w.b2, w.wsh, w.qrv);
-      svd_topk_rows<R>(w.b2, n, n, kk, V, w.alpha, w.inv, fsh, w.wsh, w.red);
+      svd_topk_rows<R>(w.b2, n, n, kk, V, w.alpha, w.inv, fsh, w.wsh, w.red, w.qrv);
     } else {
-      svd_topk_rows<R>(w.xj, rr, n, kk, V, w.alpha, w.inv, fsh, w.wsh, w.red);
+      svd_topk_rows<R>(w.xj, rr, n, kk, V, w.alpha, w.inv, fsh, w.wsh, w.red, w.qrv);
     }
     // C_j[(a,l)][k] = sum_{(q,c)} Y[(a,l)][(q,c)] V^T[k][(q,c)]
     c = ctr_init();
