@@ -53,6 +53,11 @@ def parse():
     p.add_argument("--slots", type=int, default=0)
     p.add_argument("--dt", type=float, default=1e-3)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--mode", default="vmc", choices=["vmc", "serving"],
+                   help="serving: a Poisson stream of evaluation jobs through peps_server_*")
+    p.add_argument("--arrival-s", type=float, default=30.0,
+                   help="serving: length of the arrival window per precision form")
+    p.add_argument("--rate", type=float, default=1.0, help="serving: job arrivals per second")
     p.add_argument("--no-fp64-compare", action="store_true",
                    help="skip the one-wave FP64 step timed beside the mixed form")
     return p.parse_args()
@@ -181,11 +186,80 @@ def run_reference(args, cfg):
     print(json.dumps(line), flush=True)
 
 
+SERVING_MIX = [  # (L, D, Dc, weight): lattice sizes and bonds of the serving mix, Dc = 4D
+    (8, 4, 16, 0.40), (12, 4, 16, 0.25), (12, 6, 24, 0.20), (16, 6, 24, 0.15)]
+
+
+def serving_stream(seed, rate, window_s):
+    """Seeded Poisson arrivals: (arrival time, L, D, Dc, B, tensor seed)."""
+    rng = np.random.default_rng(seed)
+    t, out = 0.0, []
+    w = np.array([m[3] for m in SERVING_MIX])
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t > window_s:
+            return out
+        L, D, Dc, _ = SERVING_MIX[rng.choice(len(SERVING_MIX), p=w / w.sum())]
+        out.append((t, L, D, Dc, int(rng.choice([64, 128, 256])), int(rng.integers(1 << 30))))
+
+
+def run_serving(args):
+    """--mode serving: the request loop under a Poisson stream, mixed form and
+    FP64 on the same arrivals; one JSON line."""
+    import torch  # noqa: F401  (CUDA context)
+
+    import paper_1806_03761_gb300 as P
+    from synth import make_peps as mk, random_sz0_configs
+    stream = serving_stream(1234, args.rate, args.arrival_s)
+    tensors = {}
+    for (_, L, D, Dc, B, sd) in stream:
+        tensors[sd] = (mk(L, D, sd % 1000, "gauss"), random_sz0_configs(L, B, sd % 997))
+    forms = ["mixed"] if args.no_fp64_compare else ["mixed", "fp64"]
+    res = {}
+    for prec in forms:
+        srv = P.PepsServer()
+        # warm-up: one small job of every shape (contexts pooled)
+        for (L, D, Dc, _) in SERVING_MIX:
+            A0 = mk(L, D, 1, "gauss")
+            srv.wait(srv.submit(A0, random_sz0_configs(L, 8, 1), L, D, Dc, prec))
+        t0 = time.perf_counter()
+        ids = []
+        for (ta, L, D, Dc, B, sd) in stream:
+            dt = ta - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            A, S = tensors[sd]
+            ids.append((srv.submit(A, S, L, D, Dc, prec), B))
+        outs = [(srv.wait(i), B) for i, B in ids]
+        srv.close()
+        lat = np.array([o["latency_s"] for o, _ in outs])
+        first = min(o["submit_s"] for o, _ in outs)
+        last = max(o["done_s"] for o, _ in outs)
+        n = sum(B for _, B in outs)
+        res[prec] = {"value": n / (last - first), "unit": "samples/s", "jobs": len(outs),
+                     "samples": n, "p50_s": float(np.percentile(lat, 50)),
+                     "p99_s": float(np.percentile(lat, 99)), "makespan_s": last - first,
+                     "errors": int(sum(o["status"] != 0 for o, _ in outs))}
+    m = res["mixed"]
+    line = {"metric": "serving: local-energy samples/s and p50/p99 request latency, Poisson job mix",
+            "value": m["value"], "unit": "samples/s", "n_gpus": 1, "steps": m["jobs"], "warmup": len(SERVING_MIX),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "ff (float-float on FP32)", "data": "synthetic",
+            "config": {"workload": "serving mix", "mix": [list(x) for x in SERVING_MIX],
+                       "samples_per_job": [64, 128, 256], "rate_per_s": args.rate,
+                       "arrival_window_s": args.arrival_s},
+            "p50_s": m["p50_s"], "p99_s": m["p99_s"], "mixed": m, "fp64": res.get("fp64")}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     cfg = dict(CONFIGS[args.workload])
     if args.impl == "reference":
         run_reference(args, cfg)
+        return
+    if args.mode == "serving":
+        run_serving(args)
         return
     import torch
 

@@ -236,6 +236,59 @@ int peps_sync_status(peps_ctx* ctx, void* stream, int32_t* flags);
  * Host call for roofline reporting; 0 for an invalid shape or `what`. */
 double peps_flops_per_sample(const peps_shape* shape, int32_t what);
 
+/* ------------------------------------------------------------------------
+ * Serving: a request loop with continuous batching.  The paper runs one
+ * large job; serving many independent VMC users at once has no counterpart
+ * there.  A server owns a worker thread on the current device.  Jobs (the
+ * amplitudes and local energies of a batch of configurations of one PEPS,
+ * of any lattice size, D, Dc and precision form) are submitted from any host
+ * thread and admitted in arrival order while the sum of the admitted jobs'
+ * device footprints (workspace, tensors, spins and outputs) stays within the
+ * HBM budget.  An admitted job gets its own context and stream and keeps its
+ * tensors and environments resident until it completes; its configurations
+ * run one wave (its slot count) at a time, so that jobs that arrive while
+ * others are on the GPU start as soon as memory allows and their waves
+ * overlap on the device.  A job's results do not depend on what runs beside
+ * it: every configuration is evaluated by the same per-sample code as
+ * peps_local_energy.
+ * ------------------------------------------------------------------------ */
+typedef struct peps_server peps_server;
+
+typedef struct {
+  peps_shape shape;       /* lattice, D, Dc, couplings, precision form */
+  const double* A;        /* host float64[N][2][D^4]; read at admission */
+  const uint8_t* spins;   /* host uint8[B][N]; read at admission */
+  int64_t B;              /* configurations, >= 1 */
+  double* e_loc;          /* host float64[B] out: E(S) */
+  double* log_abs;        /* host float64[B] out (nullable) */
+  int8_t* sign;           /* host int8[B] out (nullable) */
+} peps_job;
+
+typedef struct {
+  double submit_s, admit_s, done_s; /* host monotonic clock, seconds */
+  int64_t footprint_bytes;          /* device bytes the job held */
+  int32_t status;                   /* PEPS_OK or the job's error code */
+  int32_t flags;                    /* PEPS_FLAG_* bits seen by the job */
+} peps_job_stats;
+
+/* Create a server on the current device.  hbm_budget_bytes: device memory
+ * the admitted jobs may hold together (0 = 90 % of the free memory);
+ * slots_per_job: wave size of a job (0 = 2 per SM; a job uses
+ * min(B, slots_per_job)).  ECUDA without a device. */
+int peps_server_create(size_t hbm_budget_bytes, int32_t slots_per_job,
+                       peps_server** out);
+/* Queue a job (thread-safe).  The host buffers the job names must stay valid
+ * and untouched until peps_server_wait returns for it.  EINVAL for a bad
+ * shape or buffer, ENOMEM if the job alone exceeds the budget. */
+int peps_server_submit(peps_server* srv, const peps_job* job, int64_t* job_id);
+/* Block until job_id completes (timeout_s <= 0: no limit; ETIMEOUT when it
+ * runs out, the job keeps running).  Returns the job's status; *stats
+ * (nullable) receives its timings.  A job can be waited for once. */
+int peps_server_wait(peps_server* srv, int64_t job_id, double timeout_s,
+                     peps_job_stats* stats);
+/* Finish every queued job, stop the worker and free the server. */
+int peps_server_destroy(peps_server* srv);
+
 #ifdef __cplusplus
 }
 #endif

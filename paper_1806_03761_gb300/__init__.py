@@ -206,3 +206,60 @@ class PepsContext:
         if rc not in (0, _lib.PEPS_ENUMERIC):
             self._check(rc)
         return rc, f.value
+
+
+class PepsServer:
+    """Serving loop with continuous batching (peps_server_*): evaluation jobs
+    of any shape are admitted under an HBM budget and their waves overlap on
+    the device.  submit() returns a job id; wait() returns the job's
+    energies, log|W|, signs and timings (host numpy arrays)."""
+
+    def __init__(self, hbm_budget_bytes=0, slots_per_job=0):
+        import numpy as np
+        self.np = np
+        self.lib = _lib.load()
+        h = ctypes.c_void_p()
+        rc = self.lib.peps_server_create(int(hbm_budget_bytes), int(slots_per_job), ctypes.byref(h))
+        if rc != 0:
+            raise PepsError(rc, "peps_server_create failed")
+        self.h = h
+        self._jobs = {}
+
+    def submit(self, A, spins, L, D, Dc, precision="mixed", J1=1.0, J2=0.5):
+        np = self.np
+        A = np.ascontiguousarray(A, dtype=np.float64)
+        spins = np.ascontiguousarray(spins, dtype=np.uint8).reshape(-1, L * L)
+        B = spins.shape[0]
+        out = dict(e_loc=np.empty(B), log_abs=np.empty(B), sign=np.empty(B, dtype=np.int8))
+        job = _lib.PepsJob(_shape(L, D, Dc, J1, J2, precision), A.ctypes.data, spins.ctypes.data, B,
+                           out["e_loc"].ctypes.data, out["log_abs"].ctypes.data,
+                           out["sign"].ctypes.data)
+        jid = ctypes.c_int64(0)
+        rc = self.lib.peps_server_submit(self.h, ctypes.byref(job), ctypes.byref(jid))
+        if rc != 0:
+            raise PepsError(rc, "peps_server_submit failed")
+        self._jobs[jid.value] = (A, spins, out)  # the buffers live until wait()
+        return jid.value
+
+    def wait(self, job_id, timeout=0.0):
+        st = _lib.PepsJobStats()
+        rc = self.lib.peps_server_wait(self.h, int(job_id), float(timeout), ctypes.byref(st))
+        if rc == _lib.PEPS_ETIMEOUT:
+            raise TimeoutError("job %d still running" % job_id)
+        _, _, out = self._jobs.pop(job_id)
+        res = dict(out)
+        res.update(status=rc, flags=st.flags, submit_s=st.submit_s, admit_s=st.admit_s,
+                   done_s=st.done_s, latency_s=st.done_s - st.submit_s,
+                   footprint_bytes=st.footprint_bytes)
+        return res
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.peps_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -26,13 +26,28 @@ ERRNAMES = {0: "PEPS_OK", -1: "PEPS_EINVAL", -2: "PEPS_ENOMEM", -3: "PEPS_ECUDA"
 EXPORTS = ("peps_create", "peps_destroy", "peps_last_error", "peps_workspace_bytes", "peps_slots",
            "peps_set_tensors", "peps_amplitudes", "peps_local_energy", "peps_logderiv",
            "peps_evaluate", "peps_grad_step", "peps_sample_batch", "peps_sync_status",
-           "peps_flops_per_sample", "peps_amplitudes_noalloc", "peps_vmc_step")
+           "peps_flops_per_sample", "peps_amplitudes_noalloc", "peps_vmc_step",
+           "peps_server_create", "peps_server_submit", "peps_server_wait", "peps_server_destroy")
 
 
 class PepsShape(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int32), ("D", ctypes.c_int32), ("Dc", ctypes.c_int32),
                 ("J1", ctypes.c_double), ("J2", ctypes.c_double),
                 ("precision", ctypes.c_int32)]
+
+
+
+
+class PepsJob(ctypes.Structure):
+    _fields_ = [("shape", PepsShape), ("A", ctypes.c_void_p), ("spins", ctypes.c_void_p),
+                ("B", ctypes.c_int64), ("e_loc", ctypes.c_void_p), ("log_abs", ctypes.c_void_p),
+                ("sign", ctypes.c_void_p)]
+
+
+class PepsJobStats(ctypes.Structure):
+    _fields_ = [("submit_s", ctypes.c_double), ("admit_s", ctypes.c_double),
+                ("done_s", ctypes.c_double), ("footprint_bytes", ctypes.c_int64),
+                ("status", ctypes.c_int32), ("flags", ctypes.c_int32)]
 
 
 _lib = None
@@ -60,6 +75,10 @@ _SIGS = {
     "peps_flops_per_sample": (F64, [ctypes.POINTER(PepsShape), I32]),
     "peps_amplitudes_noalloc": (I32, [ctypes.POINTER(PepsShape), P, P, I64, P, P, P]),
     "peps_vmc_step": (I32, [P, U64, I64, I64, U64, P, P, P, P, P, P, P, I32, P, P]),
+    "peps_server_create": (I32, [ctypes.c_size_t, I32, ctypes.POINTER(P)]),
+    "peps_server_submit": (I32, [P, ctypes.POINTER(PepsJob), ctypes.POINTER(I64)]),
+    "peps_server_wait": (I32, [P, I64, F64, ctypes.POINTER(PepsJobStats)]),
+    "peps_server_destroy": (I32, [P]),
 }
 
 

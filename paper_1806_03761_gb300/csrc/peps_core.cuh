@@ -686,7 +686,7 @@ __device__ void bidiag_blocked(R* A, int m, int p, int nb, R* d, R* e, R* tau, R
 //      stays orthonormal (the truncation stays an orthogonal projection).
 // VT (kk x n) receives the vectors in decreasing order of sigma.
 // aux: >= 3 rr + 8 scalars; inv: >= kk (13 rr) scalars; fsh: 1024
-// floats of shared memory; ush: rr scalars of shared memory.
+// floats of shared memory; ush: 256 scalars of shared memory.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ unsigned peps_hash(unsigned a, unsigned b) {
   unsigned h = a * 0x9E3779B1u ^ (b + 0x7F4A7C15u) * 0x85EBCA77u;
@@ -833,19 +833,58 @@ __device__ __noinline__ void svd_topk_rows(R* X, int rr, int n, int kk, R* VT, R
     ef[i] = (i + 1 < p) ? (float)M::hi(e[i]) * rs : 0.0f;
   }
   __syncthreads();
-  for (int q = t; q < kk; q += nt) {
+  // multisection: G threads per singular value probe G points of its
+  // bracket each round (geometric spacing once the bracket excludes 0)
+  float* lo_s = fsh + 768;  // kk <= 256
+  float* hi_s = sg;
+  int* flag = reinterpret_cast<int*>(ush);
+  if (t == 0) {
     float bound = 0.0f;
     for (int i = 0; i < p; ++i)
       bound = fmaxf(bound, fabsf(df[i]) + fabsf(ef[i]) + (i > 0 ? fabsf(ef[i - 1]) : 0.0f));
-    const int idx = p - 1 - q;  // index from the smallest
-    float lo = 0.0f, hi = bound * 1.0001f + 1e-30f;
-    for (int it = 0; it < 200; ++it) {
-      float mid = (lo > 0.0f && hi > 4.0f * lo) ? sqrtf(lo) * sqrtf(hi) : 0.5f * (lo + hi);
-      if (mid <= 1e-30f) mid = 0.5f * (lo + hi);
-      if (bidiag_count(df, ef, p, mid) > idx) hi = mid; else lo = mid;
-      if (hi - lo <= 2e-7f * hi || hi < 1e-30f) break;
+    for (int q = 0; q < kk; ++q) {
+      lo_s[q] = 0.0f;
+      hi_s[q] = bound * 1.0001f + 1e-30f;
     }
-    sg[q] = 0.5f * (lo + hi);  // in units of smax
+  }
+  __syncthreads();
+  {
+    const int G = nt / kk >= 1 ? nt / kk : 1;
+    const int ngroups = nt / G;
+    for (int round = 0; round < 64; ++round) {
+      int busy = 0;
+      for (int q0 = 0; q0 < kk; q0 += ngroups) {
+        const int gq = t / G, r = t % G, q = q0 + gq;
+        const bool mine = gq < ngroups && q < kk;
+        float lo = 0.0f, hi = 0.0f;
+        bool conv = true;
+        if (mine) {
+          lo = lo_s[q];
+          hi = hi_s[q];
+          conv = hi - lo <= 2e-7f * hi || hi < 1e-30f;
+        }
+        const bool geo = lo > 0.0f && hi > 4.0f * lo;
+        int f = 0;
+        if (mine && !conv) {
+          const float fr = (float)(r + 1) / (float)(G + 1);
+          float x = geo ? lo * powf(hi / lo, fr) : lo + (hi - lo) * fr;
+          f = bidiag_count(df, ef, p, x) > p - 1 - q;
+          busy = 1;
+        }
+        flag[t] = f;
+        __syncthreads();
+        if (mine && !conv && r == 0) {
+          int r1 = 0;  // first probe above sigma_q
+          while (r1 < G && !flag[t + r1]) ++r1;
+          const float f0 = (float)r1 / (float)(G + 1), f1 = (float)(r1 + 1) / (float)(G + 1);
+          if (r1 > 0) lo_s[q] = geo ? lo * powf(hi / lo, f0) : lo + (hi - lo) * f0;
+          if (r1 < G) hi_s[q] = geo ? lo * powf(hi / lo, f1) : lo + (hi - lo) * f1;
+        }
+        __syncthreads();
+      }
+      if (!__syncthreads_or(busy)) break;
+    }
+    for (int q = t; q < kk; q += nt) sg[q] = 0.5f * (lo_s[q] + hi_s[q]);  // in units of smax
   }
   __syncthreads();
   // ---- 3. inverse iteration on the Golub-Kahan tridiagonal ----------------
@@ -853,13 +892,15 @@ __device__ __noinline__ void svd_topk_rows(R* X, int rr, int n, int kk, R* VT, R
   const int stride = 6 * N2 + p;
   const float zero_tol = (float)(M::eps() * 4.0);
   for (int q = t; q < kk; q += nt) {
-    R* U0 = inv + (int64_t)q * stride;
-    R* U1 = U0 + N2;
-    R* U2 = U1 + N2;
-    R* Lm = U2 + N2;
-    R* z = Lm + N2;
-    R* y = z + N2;
-    R* u = y + N2;
+    // private rows of the factorisation (no aliasing: the recurrences keep
+    // their carried values in registers and the loads can run ahead)
+    R* __restrict__ U0 = inv + (int64_t)q * stride;  // reciprocal pivots
+    R* __restrict__ U1 = U0 + N2;
+    R* __restrict__ U2 = U1 + N2;
+    R* __restrict__ Lm = U2 + N2;
+    R* __restrict__ z = Lm + N2;
+    R* __restrict__ y = z + N2;
+    R* __restrict__ u = y + N2;
     if (!(sg[q] > zero_tol)) {
       for (int i = 0; i < p; ++i) u[i] = M::zero();
       continue;
@@ -875,40 +916,45 @@ __device__ __noinline__ void svd_topk_rows(R* X, int rr, int n, int kk, R* VT, R
       const auto aa = fabs(M::hi(ca)), as = fabs(M::hi(gs));
       if (aa >= as) {
         R a0 = (aa == 0) ? tiny : ca;
-        R l = gs / a0;
-        U0[j] = a0; U1[j] = cb; U2[j] = cc; Lm[j] = l;
-        y[j] = M::zero();  // pivot flag 0
+        R ra = M::one() / a0;
+        R l = gs * ra;
+        U0[j] = ra; U1[j] = cb; U2[j] = cc; Lm[j] = l;
+        z[j] = M::zero();  // pivot flag 0
         R na = -mu - l * cb;
         R nb = gn - l * cc;
         ca = na; cb = nb; cc = M::zero();
       } else {
-        R l = ca / gs;
-        U0[j] = gs; U1[j] = -mu; U2[j] = gn; Lm[j] = l;
-        y[j] = M::one();  // pivot flag 1
+        R rg = M::one() / gs;
+        R l = ca * rg;
+        U0[j] = rg; U1[j] = -mu; U2[j] = gn; Lm[j] = l;
+        z[j] = M::one();  // pivot flag 1
         R na = cb + l * mu;
         R nb = cc - l * gn;
         ca = na; cb = nb; cc = M::zero();
       }
     }
-    U0[N2 - 1] = (M::hi(ca) == 0) ? tiny : ca;
+    U0[N2 - 1] = M::one() / ((M::hi(ca) == 0) ? tiny : ca);
     U1[N2 - 1] = M::zero();
     U2[N2 - 1] = M::zero();
-    // the pivot flags were staged in y: move them to z, y becomes the rhs
-    for (int j = 0; j + 1 < N2; ++j) z[j] = y[j];
     // start vector
     for (int j = 0; j < N2; ++j)
       y[j] = M::from(1.0 + (double)(peps_hash((unsigned)q, (unsigned)j) & 0xffff) * (1.0 / 65536.0));
     for (int iter = 0; iter < 3; ++iter) {
-      // forward: row interchanges and eliminations
+      // forward: row interchanges and eliminations (the running entry y[j]
+      // is carried in a register)
+      R cur = y[0];
       for (int j = 0; j + 1 < N2; ++j) {
-        if (M::hi(z[j]) != 0) { R tmp = y[j]; y[j] = y[j + 1]; y[j + 1] = tmp; }
-        y[j + 1] = y[j + 1] - Lm[j] * y[j];
+        R nxt = y[j + 1];
+        if (M::hi(z[j]) != 0) { R tmp = cur; cur = nxt; nxt = tmp; }
+        y[j] = cur;
+        cur = M::sub_mul(nxt, Lm[j], cur);
       }
+      y[N2 - 1] = cur;
       // back substitution
       R x1 = M::zero(), x2 = M::zero();
       double ymax = 0.0;
       for (int j = N2 - 1; j >= 0; --j) {
-        R xj = (y[j] - U1[j] * x1 - U2[j] * x2) / U0[j];
+        R xj = M::sub_mul(M::sub_mul(y[j], U1[j], x1), U2[j], x2) * U0[j];
         y[j] = xj;
         x2 = x1;
         x1 = xj;
@@ -920,11 +966,12 @@ __device__ __noinline__ void svd_topk_rows(R* X, int rr, int n, int kk, R* VT, R
       typename M::acc_t nrm;
       M::acc_init(nrm);
       for (int j = 0; j < N2; ++j) {
-        y[j] = y[j] * r0;
-        M::mac(nrm, y[j], y[j]);
+        const R v = y[j] * r0;
+        y[j] = v;
+        M::mac(nrm, v, v);
       }
-      const R s = M::one() / M::sqrt_(M::acc_get(nrm));
-      for (int j = 0; j < N2; ++j) y[j] = y[j] * s;
+      const R sn = M::one() / M::sqrt_(M::acc_get(nrm));
+      for (int j = 0; j < N2; ++j) y[j] = y[j] * sn;
     }
     for (int i = 0; i < p; ++i) u[i] = y[2 * i + 1];
 #undef PEPS_GK

@@ -69,3 +69,14 @@ def test_invalid_shapes_rejected_without_a_device(lib):
     s = _lib.PepsShape(4, 2, 4, 1.0, 0.5, 7)
     assert lib.peps_create(ctypes.byref(s), 0, ctypes.byref(h)) == _lib.PEPS_EINVAL
     assert lib.peps_destroy(None) == _lib.PEPS_EINVAL
+
+
+def test_server_refuses_without_a_device(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a device is present")
+    from paper_1806_03761_gb300 import _lib
+    h = ctypes.c_void_p()
+    assert lib.peps_server_create(0, 0, ctypes.byref(h)) == _lib.PEPS_ECUDA
+    assert lib.peps_server_create(0, -1, ctypes.byref(h)) == _lib.PEPS_EINVAL
+    assert lib.peps_server_destroy(None) == _lib.PEPS_EINVAL
