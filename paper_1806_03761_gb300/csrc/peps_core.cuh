@@ -303,13 +303,15 @@ __device__ void householder_r_unblocked(R* X, int m, int n, R* Rout, R* sh) {
 #define PEPS_QR_ROWS 896
 
 // Apply the panel's reflectors (explicit vectors v_s, zero above row s and
-// one at row s, in vsh with stride PEPS_QR_ROWS; taus in tau[]) to the
-// trailing columns c0..n-1 of X, rows k0..k0+mr-1.  One warp per column: the
-// column is held in registers (CAP rows per lane), every reflector is applied
-// to it in order, and it is written back once.
+// one at row s, in vsh with stride PEPS_QR_ROWS) to the trailing columns
+// c0..n-1 of X, rows k0..k0+mr-1, in the compact WY form
+// H_{nb-1} .. H_0 x = x - V T^T V^T x  (T: nb x nb upper triangular, in tt
+// with tt[r * PEPS_QR_NB + s] = T[r][s]).  One warp per column: the column is
+// held in registers (CAP rows per lane), its nb dot products with the
+// reflectors are formed together, and it is written back once.
 template <class R, int CAP>
 __device__ __forceinline__ void qr_trailing(R* X, int m, int n, int k0, int mr, int c0, int nb,
-                                            const R* vsh, const R* tau) {
+                                            const R* vsh, const R* tt) {
   typedef Arith<R> M;
   const int lane = threadIdx.x % PEPS_WARP, wid = threadIdx.x / PEPS_WARP;
   const int nw = (blockDim.x + PEPS_WARP - 1) / PEPS_WARP;
@@ -321,30 +323,49 @@ __device__ __forceinline__ void qr_trailing(R* X, int m, int n, int k0, int mr, 
       const int i = lane + q * PEPS_WARP;
       xr[q] = i < mr ? x[i] : M::zero();
     }
-    for (int s = 0; s < nb; ++s) {
-      const R ts = tau[s];
-      if (M::hi(ts) == 0) continue;
-      const R* v = vsh + s * PEPS_QR_ROWS;
-      typename M::acc_t a0, a1;
-      M::acc_init(a0);
-      M::acc_init(a1);
+    // w = V^T x
+    typename M::acc_t a[PEPS_QR_NB];
 #pragma unroll
-      for (int q = 0; q < CAP; q += 2) {
-        const int i = lane + q * PEPS_WARP;
-        if (i < mr) M::mac(a0, v[i], xr[q]);
-        if (q + 1 < CAP && i + PEPS_WARP < mr) M::mac(a1, v[i + PEPS_WARP], xr[q + 1]);
-      }
-      const R wv = ts * warp_sum<R>(M::acc_get(a0) + M::acc_get(a1));
-#pragma unroll
-      for (int q = 0; q < CAP; ++q) {
-        const int i = lane + q * PEPS_WARP;
-        if (i < mr) xr[q] = M::sub_mul(xr[q], v[i], wv);
-      }
-    }
+    for (int s = 0; s < PEPS_QR_NB; ++s) M::acc_init(a[s]);
 #pragma unroll
     for (int q = 0; q < CAP; ++q) {
       const int i = lane + q * PEPS_WARP;
-      if (i < mr) x[i] = xr[q];
+      if (i < mr) {
+#pragma unroll
+        for (int s = 0; s < PEPS_QR_NB; ++s)
+          if (s < nb) M::mac(a[s], vsh[s * PEPS_QR_ROWS + i], xr[q]);
+      }
+    }
+    R wv[PEPS_QR_NB];
+#pragma unroll
+    for (int s = 0; s < PEPS_QR_NB; ++s) wv[s] = M::acc_get(a[s]);
+#pragma unroll
+    for (int o = PEPS_WARP / 2; o > 0; o >>= 1) {
+#pragma unroll
+      for (int s = 0; s < PEPS_QR_NB; ++s) wv[s] = wv[s] + shfl_xor_r(wv[s], o);
+    }
+    // w' = T^T w
+    R wt[PEPS_QR_NB];
+#pragma unroll
+    for (int s = 0; s < PEPS_QR_NB; ++s) {
+      typename M::acc_t b;
+      M::acc_init(b);
+#pragma unroll
+      for (int r = 0; r <= s; ++r)
+        if (s < nb) M::mac(b, tt[r * PEPS_QR_NB + s], wv[r]);
+      wt[s] = M::acc_get(b);
+    }
+    // x -= V w'
+#pragma unroll
+    for (int q = 0; q < CAP; ++q) {
+      const int i = lane + q * PEPS_WARP;
+      if (i < mr) {
+        R v = xr[q];
+#pragma unroll
+        for (int s = 0; s < PEPS_QR_NB; ++s)
+          if (s < nb) v = M::sub_mul(v, vsh[s * PEPS_QR_ROWS + i], wt[s]);
+        x[i] = v;
+      }
     }
   }
 }
@@ -355,7 +376,8 @@ __device__ __forceinline__ void qr_trailing(R* X, int m, int n, int k0, int mr, 
 // shared memory, then applied to the trailing columns held in registers, so
 // that a trailing column is read and written once per panel instead of three
 // times per reflector.  vsh: PEPS_QR_NB * PEPS_QR_ROWS scalars of shared
-// memory; sh: >= 2 * PEPS_QR_NB scalars.  Falls back to the unblocked form
+// memory; sh: >= 2 * PEPS_QR_NB + 2 * PEPS_QR_NB^2 scalars.  Falls back to
+// the unblocked form
 // when m > PEPS_QR_ROWS or vsh is null.
 // ---------------------------------------------------------------------------
 template <class R>
@@ -430,12 +452,42 @@ __device__ __noinline__ void householder_r(R* X, int m, int n, R* Rout, R* sh, R
       if (i <= r) *p = (i == r) ? M::one() : M::zero();
     }
     __syncthreads();
-    // 4. the trailing columns
+    // 4. T of the compact WY form: T[s][s] = tau_s,
+    //    T[0:s, s] = -tau_s T[0:s, 0:s] (V[:, 0:s]^T v_s)
     if (k0 + nb < n) {
+      R* tt = tau + 2 * PEPS_QR_NB;  // PEPS_QR_NB^2 scalars
+      R* g = tt + PEPS_QR_NB * PEPS_QR_NB;  // v_r . v_s, r < s
+      for (int q = wid; q < nb * nb; q += nw) {
+        const int r = q / nb, c = q % nb;
+        if (r < c) {
+          typename M::acc_t a;
+          M::acc_init(a);
+          for (int i = c + lane; i < mr; i += PEPS_WARP)
+            M::mac(a, vsh[r * PEPS_QR_ROWS + i], vsh[c * PEPS_QR_ROWS + i]);
+          const R gv = warp_sum<R>(M::acc_get(a));
+          if (lane == 0) g[q] = gv;
+        }
+      }
+      __syncthreads();
+      if (t == 0) {
+        for (int c = 0; c < PEPS_QR_NB; ++c)
+          for (int r = 0; r < PEPS_QR_NB; ++r) tt[r * PEPS_QR_NB + c] = M::zero();
+        for (int c = 0; c < nb; ++c) {
+          tt[c * PEPS_QR_NB + c] = tau[c];
+          for (int r = 0; r < c; ++r) {
+            typename M::acc_t a;
+            M::acc_init(a);
+            for (int q = r; q < c; ++q) M::mac(a, tt[r * PEPS_QR_NB + q], g[q * nb + c]);
+            tt[r * PEPS_QR_NB + c] = -(tau[c] * M::acc_get(a));
+          }
+        }
+      }
+      __syncthreads();
+      // 5. the trailing columns
       if (mr <= 8 * PEPS_WARP)
-        qr_trailing<R, (8 * PEPS_WARP + PEPS_WARP - 1) / PEPS_WARP>(X, m, n, k0, mr, k0 + nb, nb, vsh, tau);
+        qr_trailing<R, (8 * PEPS_WARP + PEPS_WARP - 1) / PEPS_WARP>(X, m, n, k0, mr, k0 + nb, nb, vsh, tt);
       else
-        qr_trailing<R, (PEPS_QR_ROWS + PEPS_WARP - 1) / PEPS_WARP>(X, m, n, k0, mr, k0 + nb, nb, vsh, tau);
+        qr_trailing<R, (PEPS_QR_ROWS + PEPS_WARP - 1) / PEPS_WARP>(X, m, n, k0, mr, k0 + nb, nb, vsh, tt);
     }
     __syncthreads();
   }
