@@ -371,20 +371,162 @@ __device__ __forceinline__ void qr_trailing(R* X, int m, int n, int k0, int mr, 
 }
 
 // ---------------------------------------------------------------------------
+// Blocked form for panels taller than the register/shared-memory capacity
+// (m > PEPS_QR_ROWS): the panel of PEPS_QR_NB columns is factored in place
+// (unblocked), and the trailing columns are updated in the compact WY form
+// x -= V T^T V^T x in two streaming passes per panel (the dot products, then
+// the update), the reflectors read from the panel columns (L1-resident,
+// shared by the warps): three accesses of a trailing element per panel
+// instead of three per reflector.  sh: >= 2 PEPS_QR_NB + 2 PEPS_QR_NB^2
+// scalars of shared memory.
+// ---------------------------------------------------------------------------
+template <class R>
+__device__ void householder_r_tall(R* X, int m, int n, R* Rout, R* sh) {
+  typedef Arith<R> M;
+  const int t = threadIdx.x, lane = t % PEPS_WARP, wid = t / PEPS_WARP;
+  const int nw = (blockDim.x + PEPS_WARP - 1) / PEPS_WARP;
+  const int kmax = m < n ? m : n;
+  R* tau = sh;
+  R* tt = sh + 2 * PEPS_QR_NB;
+  R* g = tt + PEPS_QR_NB * PEPS_QR_NB;
+  for (int k0 = 0; k0 < kmax; k0 += PEPS_QR_NB) {
+    const int nb = kmax - k0 < PEPS_QR_NB ? kmax - k0 : PEPS_QR_NB;
+    // 1. the panel, unblocked, in place
+    for (int s = 0; s < nb; ++s) {
+      const int k = k0 + s;
+      R* xk = X + (int64_t)k * m;
+      if (wid == 0) {
+        typename M::acc_t a;
+        M::acc_init(a);
+        for (int i = k + 1 + lane; i < m; i += PEPS_WARP) M::mac(a, xk[i], xk[i]);
+        R xn2 = warp_sum<R>(M::acc_get(a));
+        if (lane == 0) {
+          R alpha = xk[k];
+          if (!(M::hi(xn2) > 0)) {
+            tau[s] = M::zero();
+          } else {
+            R nrm = M::sqrt_(alpha * alpha + xn2);
+            R beta = M::hi(alpha) >= 0 ? -nrm : nrm;
+            tau[s] = (beta - alpha) / beta;
+            tau[PEPS_QR_NB] = M::one() / (alpha - beta);
+            xk[k] = beta;
+          }
+        }
+        __syncwarp();
+        const R scl = tau[PEPS_QR_NB];
+        if (M::hi(tau[s]) != 0)
+          for (int i = k + 1 + lane; i < m; i += PEPS_WARP) xk[i] = xk[i] * scl;
+        else
+          for (int i = k + 1 + lane; i < m; i += PEPS_WARP) xk[i] = M::zero();
+      }
+      __syncthreads();
+      if (M::hi(tau[s]) != 0) reflect_columns<R>(X, m, k, k + 1, k0 + nb, xk, tau[s]);
+      __syncthreads();
+    }
+    if (k0 + nb >= n) continue;
+    // 2. T of the compact WY form (v_r: one at row k0+r, the stored tail
+    //    below, zeros above)
+    for (int q = wid; q < nb * nb; q += nw) {
+      const int r = q / nb, c = q % nb;
+      if (r < c) {
+        const R* vr = X + (int64_t)(k0 + r) * m;
+        const R* vc = X + (int64_t)(k0 + c) * m;
+        typename M::acc_t a;
+        M::acc_init(a);
+        if (lane == 0) M::mac(a, vr[k0 + c], M::one());
+        for (int i = k0 + c + 1 + lane; i < m; i += PEPS_WARP) M::mac(a, vr[i], vc[i]);
+        const R gv = warp_sum<R>(M::acc_get(a));
+        if (lane == 0) g[q] = gv;
+      }
+    }
+    __syncthreads();
+    if (t == 0) {
+      for (int c = 0; c < PEPS_QR_NB; ++c)
+        for (int r = 0; r < PEPS_QR_NB; ++r) tt[r * PEPS_QR_NB + c] = M::zero();
+      for (int c = 0; c < nb; ++c) {
+        tt[c * PEPS_QR_NB + c] = tau[c];
+        for (int r = 0; r < c; ++r) {
+          typename M::acc_t a;
+          M::acc_init(a);
+          for (int q = r; q < c; ++q) M::mac(a, tt[r * PEPS_QR_NB + q], g[q * nb + c]);
+          tt[r * PEPS_QR_NB + c] = -(tau[c] * M::acc_get(a));
+        }
+      }
+    }
+    __syncthreads();
+    // 3. the trailing columns, one warp each, two passes
+    for (int c = k0 + nb + wid; c < n; c += nw) {
+      R* x = X + (int64_t)c * m;
+      typename M::acc_t a[PEPS_QR_NB];
+#pragma unroll
+      for (int s = 0; s < PEPS_QR_NB; ++s) M::acc_init(a[s]);
+      for (int i = k0 + lane; i < m; i += PEPS_WARP) {
+        const R xi = x[i];
+#pragma unroll
+        for (int s = 0; s < PEPS_QR_NB; ++s) {
+          if (s < nb && i >= k0 + s) {
+            const R v = i == k0 + s ? M::one() : X[(int64_t)(k0 + s) * m + i];
+            M::mac(a[s], v, xi);
+          }
+        }
+      }
+      R wv[PEPS_QR_NB];
+#pragma unroll
+      for (int s = 0; s < PEPS_QR_NB; ++s) wv[s] = M::acc_get(a[s]);
+#pragma unroll
+      for (int o = PEPS_WARP / 2; o > 0; o >>= 1) {
+#pragma unroll
+        for (int s = 0; s < PEPS_QR_NB; ++s) wv[s] = wv[s] + shfl_xor_r(wv[s], o);
+      }
+      R wt[PEPS_QR_NB];
+#pragma unroll
+      for (int s = 0; s < PEPS_QR_NB; ++s) {
+        typename M::acc_t b;
+        M::acc_init(b);
+#pragma unroll
+        for (int r = 0; r <= s; ++r)
+          if (s < nb) M::mac(b, tt[r * PEPS_QR_NB + s], wv[r]);
+        wt[s] = M::acc_get(b);
+      }
+      for (int i = k0 + lane; i < m; i += PEPS_WARP) {
+        R xi = x[i];
+#pragma unroll
+        for (int s = 0; s < PEPS_QR_NB; ++s) {
+          if (s < nb && i >= k0 + s) {
+            const R v = i == k0 + s ? M::one() : X[(int64_t)(k0 + s) * m + i];
+            xi = M::sub_mul(xi, v, wt[s]);
+          }
+        }
+        x[i] = xi;
+      }
+    }
+    __syncthreads();
+  }
+  for (int o = t; o < kmax * n; o += blockDim.x) {
+    int i = o / n, c = o % n;
+    Rout[o] = (c >= i) ? X[(int64_t)c * m + i] : M::zero();
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
 // Blocked form of householder_r (the same reflectors, applied in the same
 // order to every column): panels of PEPS_QR_NB columns are factored in
 // shared memory, then applied to the trailing columns held in registers, so
 // that a trailing column is read and written once per panel instead of three
 // times per reflector.  vsh: PEPS_QR_NB * PEPS_QR_ROWS scalars of shared
-// memory; sh: >= 2 * PEPS_QR_NB + 2 * PEPS_QR_NB^2 scalars.  Falls back to
-// the unblocked form
-// when m > PEPS_QR_ROWS or vsh is null.
+// memory; sh: >= 2 * PEPS_QR_NB + 2 * PEPS_QR_NB^2 scalars.  Panels taller
+// than PEPS_QR_ROWS take householder_r_tall; a null vsh the unblocked form.
 // ---------------------------------------------------------------------------
 template <class R>
 __device__ __noinline__ void householder_r(R* X, int m, int n, R* Rout, R* sh, R* vsh) {
   typedef Arith<R> M;
-  if (vsh == nullptr || m > PEPS_QR_ROWS) {
+  if (vsh == nullptr) {
     householder_r_unblocked<R>(X, m, n, Rout, sh);
+    return;
+  }
+  if (m > PEPS_QR_ROWS) {
+    householder_r_tall<R>(X, m, n, Rout, sh);
     return;
   }
   const int t = threadIdx.x, lane = t % PEPS_WARP, wid = t / PEPS_WARP;
@@ -719,6 +861,11 @@ __device__ void bidiag_blocked(R* A, int m, int p, int nb, R* d, R* e, R* tau, R
   }
 }
 
+// Arithmetic of the inverse-iteration recurrences: FP64 unless the form is
+// FP32 (its workspace is sized in FP32 words).
+template <class R> struct InvType { typedef double T; };
+template <> struct InvType<float> { typedef float T; };
+
 // ---------------------------------------------------------------------------
 // Top-kk right singular vectors of X (rr x n row-major, 1 <= rr <= n) by
 // Golub-Kahan bidiagonalisation, bisection and inverse iteration:
@@ -728,7 +875,7 @@ __device__ void bidiag_blocked(R* A, int m, int p, int nb, R* d, R* e, R* tau, R
 //   2. The kk largest singular values of B by bisection on the count of
 //      singular values below x, from the stationary qd transform of
 //      B^T B - x^2 (relative accuracy in FP32; Demmel-Kahan).
-//   3. For each, inverse iteration in the form's arithmetic on the
+//   3. For each, inverse iteration (FP64; FP32 in the FP32 form) on the
 //      Golub-Kahan tridiagonal (zero diagonal, off-diagonals d0,e0,d1,...),
 //      whose eigenvector for +sigma interleaves (v_0, u_0, v_1, u_1, ...) with
 //      B v = sigma u; three solves with a partially pivoted LU.
@@ -943,89 +1090,92 @@ __device__ __noinline__ void svd_topk_rows(R* X, int rr, int n, int kk, R* VT, R
   const int N2 = 2 * p;
   const int stride = 6 * N2 + p;
   const float zero_tol = (float)(M::eps() * 4.0);
+  // The recurrences below are serial in j, 24-odd lanes wide and bound by
+  // latency, not throughput: they run in FP64 for the FP64 and float-float
+  // forms (shorter dependency chains than float-float, and more accurate),
+  // in FP32 for the FP32 form.
+  typedef typename InvType<R>::T T;
   for (int q = t; q < kk; q += nt) {
     // private rows of the factorisation (no aliasing: the recurrences keep
     // their carried values in registers and the loads can run ahead)
-    R* __restrict__ U0 = inv + (int64_t)q * stride;  // reciprocal pivots
-    R* __restrict__ U1 = U0 + N2;
-    R* __restrict__ U2 = U1 + N2;
-    R* __restrict__ Lm = U2 + N2;
-    R* __restrict__ z = Lm + N2;
-    R* __restrict__ y = z + N2;
-    R* __restrict__ u = y + N2;
+    T* __restrict__ U0 = reinterpret_cast<T*>(inv + (int64_t)q * stride);  // reciprocal pivots
+    T* __restrict__ U1 = U0 + N2;
+    T* __restrict__ U2 = U1 + N2;
+    T* __restrict__ Lm = U2 + N2;
+    T* __restrict__ z = Lm + N2;
+    T* __restrict__ y = z + N2;
+    R* __restrict__ u = inv + (int64_t)q * stride + 6 * N2;
     if (!(sg[q] > zero_tol)) {
       for (int i = 0; i < p; ++i) u[i] = M::zero();
       continue;
     }
-    const R mu = M::from((double)sg[q] * smax);
-    const R tiny = M::from(smax * 1e-30 + 1e-300);
+    const T mu = (T)((double)sg[q] * smax);
+    const T tiny = (T)(smax * 1e-30 + 1e-300);
     // g_j: off-diagonal j of the Golub-Kahan matrix
-#define PEPS_GK(j) (((j) & 1) ? e[(j) >> 1] : d[(j) >> 1])
-    R ca = -mu, cb = PEPS_GK(0), cc = M::zero();
+#define PEPS_GK(j) ((T)M::to(((j) & 1) ? e[(j) >> 1] : d[(j) >> 1]))
+    T ca = -mu, cb = PEPS_GK(0), cc = 0;
     for (int j = 0; j + 1 < N2; ++j) {
-      const R gs = PEPS_GK(j);
-      const R gn = (j + 2 < N2) ? PEPS_GK(j + 1) : M::zero();
-      const auto aa = fabs(M::hi(ca)), as = fabs(M::hi(gs));
-      if (aa >= as) {
-        R a0 = (aa == 0) ? tiny : ca;
-        R ra = M::one() / a0;
-        R l = gs * ra;
+      const T gs = PEPS_GK(j);
+      const T gn = (j + 2 < N2) ? PEPS_GK(j + 1) : (T)0;
+      if (fabs(ca) >= fabs(gs)) {
+        const T a0 = (ca == 0) ? tiny : ca;
+        const T ra = (T)1 / a0;
+        const T l = gs * ra;
         U0[j] = ra; U1[j] = cb; U2[j] = cc; Lm[j] = l;
-        z[j] = M::zero();  // pivot flag 0
-        R na = -mu - l * cb;
-        R nb = gn - l * cc;
-        ca = na; cb = nb; cc = M::zero();
+        z[j] = 0;  // pivot flag 0
+        ca = -mu - l * cb;
+        cb = gn - l * cc;
       } else {
-        R rg = M::one() / gs;
-        R l = ca * rg;
+        const T rg = (T)1 / gs;
+        const T l = ca * rg;
         U0[j] = rg; U1[j] = -mu; U2[j] = gn; Lm[j] = l;
-        z[j] = M::one();  // pivot flag 1
-        R na = cb + l * mu;
-        R nb = cc - l * gn;
-        ca = na; cb = nb; cc = M::zero();
+        z[j] = 1;  // pivot flag 1
+        const T na = cb + l * mu;
+        cb = cc - l * gn;
+        ca = na;
       }
+      cc = 0;
     }
-    U0[N2 - 1] = M::one() / ((M::hi(ca) == 0) ? tiny : ca);
-    U1[N2 - 1] = M::zero();
-    U2[N2 - 1] = M::zero();
+    U0[N2 - 1] = (T)1 / ((ca == 0) ? tiny : ca);
+    U1[N2 - 1] = 0;
+    U2[N2 - 1] = 0;
     // start vector
     for (int j = 0; j < N2; ++j)
-      y[j] = M::from(1.0 + (double)(peps_hash((unsigned)q, (unsigned)j) & 0xffff) * (1.0 / 65536.0));
+      y[j] = (T)(1.0 + (double)(peps_hash((unsigned)q, (unsigned)j) & 0xffff) * (1.0 / 65536.0));
     for (int iter = 0; iter < 3; ++iter) {
-      // forward: row interchanges and eliminations (the running entry y[j]
-      // is carried in a register)
-      R cur = y[0];
+      // forward: row interchanges and eliminations (the running entry is
+      // carried in a register)
+      T cur = y[0];
+#pragma unroll 4
       for (int j = 0; j + 1 < N2; ++j) {
-        R nxt = y[j + 1];
-        if (M::hi(z[j]) != 0) { R tmp = cur; cur = nxt; nxt = tmp; }
+        T nxt = y[j + 1];
+        if (z[j] != 0) { const T tmp = cur; cur = nxt; nxt = tmp; }
         y[j] = cur;
-        cur = M::sub_mul(nxt, Lm[j], cur);
+        cur = nxt - Lm[j] * cur;
       }
       y[N2 - 1] = cur;
       // back substitution
-      R x1 = M::zero(), x2 = M::zero();
-      double ymax = 0.0;
+      T x1 = 0, x2 = 0, ymax = 0;
+#pragma unroll 4
       for (int j = N2 - 1; j >= 0; --j) {
-        R xj = M::sub_mul(M::sub_mul(y[j], U1[j], x1), U2[j], x2) * U0[j];
+        const T xj = (y[j] - U1[j] * x1 - U2[j] * x2) * U0[j];
         y[j] = xj;
         x2 = x1;
         x1 = xj;
-        ymax = fmax(ymax, fabs((double)M::hi(xj)));
+        ymax = fmax(ymax, fabs(xj));
       }
-      // scale to unit max-abs before the norm (the squares could leave the
-      // FP32 exponent range in the float-float form), then to unit norm
-      const R r0 = M::from(ymax > 0.0 ? 1.0 / ymax : 1.0);
-      typename M::acc_t nrm;
-      M::acc_init(nrm);
+      // to unit max-abs, then to unit norm
+      const T r0 = ymax > 0 ? (T)1 / ymax : (T)1;
+      T nrm = 0;
       for (int j = 0; j < N2; ++j) {
-        const R v = y[j] * r0;
+        const T v = y[j] * r0;
         y[j] = v;
-        M::mac(nrm, v, v);
+        nrm += v * v;
       }
-      const R sn = M::one() / M::sqrt_(M::acc_get(nrm));
+      const T sn = (T)1 / sqrt(nrm);
       for (int j = 0; j < N2; ++j) y[j] = y[j] * sn;
     }
-    for (int i = 0; i < p; ++i) u[i] = y[2 * i + 1];
+    for (int i = 0; i < p; ++i) u[i] = M::from((double)y[2 * i + 1]);
 #undef PEPS_GK
   }
   __syncthreads();

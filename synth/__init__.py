@@ -88,6 +88,8 @@ CONFIGS = {
                         config_seed=3, batch=4096),
     "16x16_D6_Dc24": dict(L=16, D=6, Dc=24, recipe="gauss", seed=4,
                           config_seed=5, batch=8192),
+    "24x24_D8_Dc32": dict(L=24, D=8, Dc=32, recipe="gauss", seed=6,
+                          config_seed=7, batch=1024),
 }
 
 

@@ -145,6 +145,15 @@ def test_parity_16x16_D6_Dc24(prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_parity_6x6_D8_Dc32_tall_panels(prec):
+    # D*Dc = 256: the QR sweep's panels reach 2048 x 256 (the tall blocked
+    # path) and the SVDs 256 x 256
+    A = make_peps(6, 8, seed=6)
+    spins = random_sz0_configs(6, 2, seed=7)
+    check_eval(A, spins, 6, 8, 32, prec, delta=False)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_amplitudes_and_logderiv_entry_points(prec):
     L, D, Dc = 5, 2, 4
     tol = TOL[prec]
