@@ -392,7 +392,9 @@ def main():
                "sample": "1 chain x 1 Metropolis sweep + full evaluation (E, Delta)"}
     lat = sorted(step_ms)
     h2d, d2h = B * N, B * N + B * 8 + 8
-    line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world,
+    metric = METRIC if args.workload == WORKLOAD else \
+        "local-energy samples/s at %dx%d D=%d Dc=%d (fused VMC step)" % (L, L, D, Dc)
+    line = {"metric": metric, "value": value, "unit": "samples/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dev_ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"mixed": "ff (float-float on FP32)", "fp64": "f64", "fp32": "f32"}[args.precision],
