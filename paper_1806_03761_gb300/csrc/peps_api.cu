@@ -145,7 +145,7 @@ int default_slots() {
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  return 2 * sms;
+  return PEPS_MINB * sms;
 }
 
 template <class R>

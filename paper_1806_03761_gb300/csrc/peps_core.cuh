@@ -87,11 +87,17 @@ __device__ __forceinline__ Ctr ctr_init() {
 // read through the coherent path (no __restrict__ / read-only cache).
 //
 // Register blocking: when the output has a digit carried only by A (dA) and
-// one carried only by B (dB), each thread computes the 2 x 2 outputs
-// (2x, 2x+1) x (2y, 2y+1) over those digits, so that every loaded element of
-// either operand feeds two multiply-adds.  Otherwise each thread computes two
+// one carried only by B (dB), each thread computes a BA x 2 block of outputs
+// over those digits, so that every loaded element of A feeds two and every
+// loaded element of B BA multiply-adds (the summation order of each output
+// is unchanged).  Otherwise each thread computes two
 // outputs adjacent in the fastest digit (shared loads where an operand does
 // not carry it).
+// Outputs per thread along the A-only digit: 4 for the FP32-word forms, 2 for
+// FP64 (whose accumulators take twice the registers; measured slower at 4).
+template <class R> struct ContractBlock { static constexpr int BA = 4; };
+template <> struct ContractBlock<double> { static constexpr int BA = 2; };
+
 template <class R>
 __device__ void contract(const Ctr& d, const R* A, const R* B, R* C) {
   typedef Arith<R> M;
@@ -102,13 +108,14 @@ __device__ void contract(const Ctr& d, const R* A, const R* B, R* C) {
     if (d.e[i] > 1 && d.sb[i] != 0 && d.sa[i] == 0) dB = i;
   }
   if (dA >= 0 && dB >= 0) {
+    // BA x BB outputs per thread over (dA, dB)
+    constexpr int BA = ContractBlock<R>::BA, BB = 2;
     int eb[5];
     int tot = 1;
     int sA = 0, sB = 0, cA = 0, cB = 0, nA = 1, nB = 1;
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
-      const bool bl = (i == dA) || (i == dB);
-      eb[i] = bl ? (d.e[i] + 1) >> 1 : d.e[i];
+      eb[i] = (i == dA) ? (d.e[i] + BA - 1) / BA : (i == dB) ? (d.e[i] + BB - 1) / BB : d.e[i];
       tot *= eb[i];
       if (i == dA) { sA = d.sa[i]; cA = d.sc[i]; nA = d.e[i]; }
       if (i == dB) { sB = d.sb[i]; cB = d.sc[i]; nB = d.e[i]; }
@@ -120,35 +127,43 @@ __device__ void contract(const Ctr& d, const R* A, const R* B, R* C) {
       for (int i = 4; i >= 0; --i) {
         int q = t % eb[i];
         t /= eb[i];
-        if (i == dA) { q *= 2; xA = q; }
-        if (i == dB) { q *= 2; xB = q; }
+        if (i == dA) { q *= BA; xA = q; }
+        if (i == dB) { q *= BB; xB = q; }
         oa += q * d.sa[i];
         ob += q * d.sb[i];
         oc += q * d.sc[i];
       }
-      const bool vA = xA + 1 < nA, vB = xB + 1 < nB;
-      const int da = vA ? sA : 0, db = vB ? sB : 0;
-      typename M::acc_t c00, c01, c10, c11;
-      M::acc_init(c00);
-      M::acc_init(c01);
-      M::acc_init(c10);
-      M::acc_init(c11);
+      // rows beyond the extent repeat the last valid one (computed, not stored)
+      int da[BA], db[BB];
+#pragma unroll
+      for (int x = 0; x < BA; ++x) da[x] = (xA + x < nA ? x : nA - 1 - xA) * sA;
+#pragma unroll
+      for (int y = 0; y < BB; ++y) db[y] = (xB + y < nB ? y : nB - 1 - xB) * sB;
+      typename M::acc_t c[BA][BB];
+#pragma unroll
+      for (int x = 0; x < BA; ++x)
+#pragma unroll
+        for (int y = 0; y < BB; ++y) M::acc_init(c[x][y]);
       for (int k1 = 0; k1 < d.k1; ++k1) {
         const R* pa = A + oa + k1 * d.ka1;
         const R* pb = B + ob + k1 * d.kb1;
         for (int k2 = 0; k2 < d.k2; ++k2) {
-          const R a0 = pa[k2 * d.ka2], a1 = pa[k2 * d.ka2 + da];
-          const R b0 = pb[k2 * d.kb2], b1 = pb[k2 * d.kb2 + db];
-          M::mac(c00, a0, b0);
-          M::mac(c01, a0, b1);
-          M::mac(c10, a1, b0);
-          M::mac(c11, a1, b1);
+          R av[BA], bv[BB];
+#pragma unroll
+          for (int x = 0; x < BA; ++x) av[x] = pa[k2 * d.ka2 + da[x]];
+#pragma unroll
+          for (int y = 0; y < BB; ++y) bv[y] = pb[k2 * d.kb2 + db[y]];
+#pragma unroll
+          for (int x = 0; x < BA; ++x)
+#pragma unroll
+            for (int y = 0; y < BB; ++y) M::mac(c[x][y], av[x], bv[y]);
         }
       }
-      C[oc] = M::acc_get(c00);
-      if (vB) C[oc + cB] = M::acc_get(c01);
-      if (vA) C[oc + cA] = M::acc_get(c10);
-      if (vA && vB) C[oc + cA + cB] = M::acc_get(c11);
+#pragma unroll
+      for (int x = 0; x < BA; ++x)
+#pragma unroll
+        for (int y = 0; y < BB; ++y)
+          if (xA + x < nA && xB + y < nB) C[oc + x * cA + y * cB] = M::acc_get(c[x][y]);
     }
     __syncthreads();
     return;

@@ -390,7 +390,7 @@ __device__ __forceinline__ void evaluate_one(const EvalArgs<R>& a, int64_t b, Bl
 }
 
 template <class R>
-__global__ void __launch_bounds__(PEPS_NT, 2) peps_eval_kernel(EvalArgs<R> a) {
+__global__ void __launch_bounds__(PEPS_NT, PEPS_MINB) peps_eval_kernel(EvalArgs<R> a) {
   __shared__ BlockShared<R> sh;
   const PepsPlan& P = a.P;
   const int N = P.N, D4 = P.D4;

@@ -42,7 +42,7 @@ __global__ void noalloc_put_steps(NoallocSteps st, int n, PepsStep* dst, int* fl
 
 // The amplitude-only variant of the evaluation kernel: lower environments,
 // then the row-0 strip closed against Dn_1 (Eq. PEPS; Fig. 1(b,c)).
-__global__ void __launch_bounds__(PEPS_NT, 2) peps_amp_noalloc_kernel(EvalArgs<double> a) {
+__global__ void __launch_bounds__(PEPS_NT, PEPS_MINB) peps_amp_noalloc_kernel(EvalArgs<double> a) {
   __shared__ double red[PEPS_NT];
   __shared__ __align__(16) unsigned char redR_raw[PEPS_NT * sizeof(double)];
   __shared__ __align__(16) unsigned char wsh_raw[256 * sizeof(double)];
@@ -193,7 +193,7 @@ extern "C" int peps_amplitudes_noalloc(const peps_shape* shape, const double* A,
   if (cudaGetDevice(&dev) != cudaSuccess) return PEPS_ECUDA;
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return PEPS_ECUDA;
-  const int nslots = (int)std::min<int64_t>(std::min<int64_t>(fit, 2 * (int64_t)sms), B);
+  const int nslots = (int)std::min<int64_t>(std::min<int64_t>(fit, PEPS_MINB * (int64_t)sms), B);
   unsigned char* base = nullptr;
   if (scratch_address(dev, (void**)&base) != cudaSuccess) return PEPS_ECUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);

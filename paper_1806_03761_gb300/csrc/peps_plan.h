@@ -14,6 +14,12 @@
 #pragma once
 #include <stdint.h>
 
+// Resident blocks per SM the kernels' register budget is set for (their
+// __launch_bounds__); the default slot count is this many per SM.
+#ifndef PEPS_MINB
+#define PEPS_MINB 2
+#endif
+
 #define PEPS_MAXL 32
 
 struct PepsStep {

@@ -170,7 +170,7 @@ __device__ void load_chain(BlockShared<R>& sh, const uint8_t* state, int64_t c, 
 }
 
 template <class R>
-__global__ void __launch_bounds__(PEPS_NT, 2) peps_sample_kernel(SampleArgs<R> a) {
+__global__ void __launch_bounds__(PEPS_NT, PEPS_MINB) peps_sample_kernel(SampleArgs<R> a) {
   __shared__ BlockShared<R> sh;
   const PepsPlan& P = a.P;
   const int N = P.N;
@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(PEPS_NT, 2) peps_sample_kernel(SampleArgs<R> a
 // peps_eval_kernel), then one Metropolis sweep (as peps_sample_kernel)
 // that reuses the lower environments the evaluation built.
 template <class R>
-__global__ void __launch_bounds__(PEPS_NT, 2) peps_vmc_kernel(EvalArgs<R> a, SampleArgs<R> s) {
+__global__ void __launch_bounds__(PEPS_NT, PEPS_MINB) peps_vmc_kernel(EvalArgs<R> a, SampleArgs<R> s) {
   __shared__ BlockShared<R> sh;
   const PepsPlan& P = a.P;
   const int N = P.N, D4 = P.D4;
