@@ -225,7 +225,6 @@ struct BlockShared {
   __align__(16) unsigned char wsh_raw[256 * sizeof(R)];
   __align__(16) unsigned char qrv_raw[PEPS_QR_NB * PEPS_QR_ROWS * sizeof(R)];
   double rot[512];
-  int ish[264];
   uint8_t sp[PEPS_MAXL * PEPS_MAXL];
   double dnlog[PEPS_MAXL + 1];
   double uplog[3];
@@ -240,7 +239,6 @@ __device__ Work<R> bind_work(const PepsPlan& P, R* ws, double* wsd, BlockShared<
   w.wsh = reinterpret_cast<R*>(sh.wsh_raw);
   w.qrv = reinterpret_cast<R*>(sh.qrv_raw);
   w.rot = sh.rot;
-  w.ish = sh.ish;
   w.flags = flags;
   return w;
 }

@@ -40,7 +40,6 @@ struct Work {
   R* wsh;
   R* qrv;  // PEPS_QR_NB * PEPS_QR_ROWS: the blocked QR's panel (null: unblocked)
   double* rot;
-  int* ish;
   int* flags;
 };
 

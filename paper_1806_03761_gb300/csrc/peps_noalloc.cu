@@ -48,7 +48,6 @@ __global__ void __launch_bounds__(PEPS_NT, PEPS_MINB) peps_amp_noalloc_kernel(Ev
   __shared__ __align__(16) unsigned char wsh_raw[256 * sizeof(double)];
   __shared__ __align__(16) unsigned char qrv_raw[PEPS_QR_NB * PEPS_QR_ROWS * sizeof(double)];
   __shared__ double rot[512];
-  __shared__ int ish[264];
   __shared__ uint8_t sp[PEPS_MAXL * PEPS_MAXL];
   __shared__ double dnlog[PEPS_MAXL + 1];
   const PepsPlan& P = a.P;
@@ -59,7 +58,6 @@ __global__ void __launch_bounds__(PEPS_NT, PEPS_MINB) peps_amp_noalloc_kernel(Ev
   w.wsh = reinterpret_cast<double*>(wsh_raw);
   w.qrv = reinterpret_cast<double*>(qrv_raw);
   w.rot = rot;
-  w.ish = ish;
   w.flags = a.flags;
   for (int64_t b = blockIdx.x; b < a.B; b += gridDim.x) {
     for (int m = threadIdx.x; m < N; m += blockDim.x) sp[m] = a.spins[b * N + m];
