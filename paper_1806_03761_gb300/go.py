@@ -96,7 +96,8 @@ class GOLoop:
 
     # -- checkpoint / resume ------------------------------------------------
     def save(self, path):
-        self.torch.cuda.synchronize()
+        if self.A.is_cuda:
+            self.torch.cuda.synchronize()
         c = self.ctx
         state = (self.state.cpu().numpy() if self.state is not None
                  else np.zeros((0, c.N), np.uint8))
@@ -112,7 +113,7 @@ class GOLoop:
         os.replace(tmp, path)
 
     @classmethod
-    def load(cls, path, ctx=None, slots=0):
+    def load(cls, path, ctx=None, slots=0, device="cuda"):
         """Restore a loop; ctx (optional) must have the saved shape."""
         import torch
         z = np.load(path)
@@ -124,10 +125,10 @@ class GOLoop:
             raise ValueError("checkpoint shape %s does not match the context" % ((L, D, Dc, prec),))
         step, sweep, seed, n_chains, spc, n_burn, off, world = (int(x) for x in z["counters"])
         dt0, decay, tol = (float(x) for x in z["hyper"])
-        A = torch.from_numpy(z["A"]).cuda()
+        A = torch.from_numpy(z["A"]).to(device)
         loop = cls(ctx, A, seed, n_chains, spc, n_burn, dt0, decay, tol, off, world)
         loop.step, loop.sweep = step, sweep
         loop.energies = [float(x) for x in z["energies"]]
         if z["state"].shape[0]:
-            loop.state = torch.from_numpy(z["state"]).cuda().contiguous()
+            loop.state = torch.from_numpy(z["state"]).to(device).contiguous()
         return loop

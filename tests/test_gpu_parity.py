@@ -144,6 +144,46 @@ def test_parity_16x16_D6_Dc24(prec):
     check_eval(A, spins, 16, 6, 24, prec, conditioned=True)
 
 
+def test_full_wave_16x16_in_the_bench_launch():
+    # the bench's launch configuration: one wave of 304 chains on the default
+    # slots, both forms; every output compared across forms (a property at
+    # any size) and three sampled outputs against the oracle
+    L, D, Dc, B = 16, 6, 24, 304
+    A = make_peps(L, D, seed=4)
+    spins = random_sz0_configs(L, B, seed=5)
+    sp = torch.from_numpy(spins).cuda()
+    res = {}
+    for prec in ("fp64", "mixed"):
+        ctx = ctx_for(L, D, Dc, prec)
+        assert ctx.slots >= B
+        ctx.set_tensors(torch.from_numpy(A).cuda())
+        r = ctx.local_energy(sp)
+        rc, flags = ctx.sync_status()
+        assert rc == 0, flags
+        res[prec] = {k: r[k].cpu().numpy() for k in ("e_loc", "log_abs", "sign")}
+        ctx.close()
+    e64, emx = res["fp64"]["e_loc"], res["mixed"]["e_loc"]
+    assert np.array_equal(res["fp64"]["sign"], res["mixed"]["sign"])
+    de = np.abs(emx - e64) / np.maximum(1.0, np.abs(e64))
+    print("mixed vs fp64 over the wave: max %.2e median %.2e" % (de.max(), np.median(de)))
+    assert de.max() <= TOL["mixed"]
+    assert np.max(np.abs(res["mixed"]["log_abs"] - res["fp64"]["log_abs"])) <= TOL["mixed"]
+    rng = np.random.default_rng(1234)
+    Ap = A * (1.0 + 2.0 ** -52 * rng.standard_normal(A.shape))
+    for b in (0, 151, 303):
+        o = oracle.evaluate(A, spins[b], L, Dc)
+        op = oracle.evaluate(Ap, spins[b], L, Dc)
+        s_e = abs(op["e_loc"] - o["e_loc"]) / max(1.0, abs(o["e_loc"]))
+        s_l = abs(op["log_abs"] - o["log_abs"])
+        for prec in ("fp64", "mixed"):
+            assert res[prec]["sign"][b] == o["sign"]
+            ge = abs(res[prec]["e_loc"][b] - o["e_loc"]) / max(1.0, abs(o["e_loc"]))
+            gl = abs(res[prec]["log_abs"][b] - o["log_abs"])
+            be, bl = max(TOL[prec], 100.0 * s_e), max(TOL[prec], 100.0 * s_l)
+            print(prec, b, "e %.2e (bound %.2e)  log|W| %.2e (bound %.2e)" % (ge, be, gl, bl))
+            assert ge <= be and gl <= bl
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_parity_6x6_D8_Dc32_tall_panels(prec):
     # D*Dc = 256: the QR sweep's panels reach 2048 x 256 (the tall blocked
