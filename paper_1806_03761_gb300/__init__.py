@@ -246,6 +246,8 @@ class PepsServer:
         rc = self.lib.peps_server_wait(self.h, int(job_id), float(timeout), ctypes.byref(st))
         if rc == _lib.PEPS_ETIMEOUT:
             raise TimeoutError("job %d still running" % job_id)
+        if job_id not in self._jobs:
+            raise PepsError(rc, "unknown job id %d (or already waited for)" % job_id)
         _, _, out = self._jobs.pop(job_id)
         res = dict(out)
         res.update(status=rc, flags=st.flags, submit_s=st.submit_s, admit_s=st.admit_s,
