@@ -1224,25 +1224,61 @@ __device__ __noinline__ void svd_topk_rows(R* X, int rr, int n, int kk, R* VT, R
     for (int i = t; i < p; i += nt) uq[i] = uq[i] * s;
     __syncthreads();
   }
-  // ---- 4b. V_i = Q [u_i; 0] (reflectors in reverse order), one warp each --
-  for (int q = wid; q < kk; q += nw) {
-    R* v = VT + (int64_t)q * n;
-    const R* uq = inv + (int64_t)q * stride + 6 * N2;
-    for (int i = lane; i < n; i += PEPS_WARP) v[i] = (i < p) ? uq[i] : M::zero();
+  // ---- 4b. V_i = Q [u_i; 0] (reflectors in reverse order): each warp
+  //      transforms up to three vectors together (one load of the reflector
+  //      per element for all three, interleaved reductions)
+  for (int q0 = wid; q0 < kk; q0 += 3 * nw) {
+    R* vv[3];
+    bool on[3];
+#pragma unroll
+    for (int g = 0; g < 3; ++g) {
+      const int q = q0 + g * nw;
+      on[g] = q < kk;
+      vv[g] = VT + (int64_t)(on[g] ? q : q0) * n;
+      if (on[g]) {
+        const R* uq = inv + (int64_t)q * stride + 6 * N2;
+        for (int i = lane; i < n; i += PEPS_WARP) vv[g][i] = (i < p) ? uq[i] : M::zero();
+      }
+    }
     __syncwarp();
-    if (!(sg[q] > zero_tol)) continue;
     for (int k = p - 1; k >= 0; --k) {
       const R tk = tau[k];
       if (M::hi(tk) == 0) continue;
       const R* ck = X + (int64_t)k * n;
-      typename M::acc_t a;
-      M::acc_init(a);
-      if (lane == 0) M::mac(a, M::one(), v[k]);
-      for (int i = k + 1 + lane; i < n; i += PEPS_WARP) M::mac(a, ck[i], v[i]);
-      const R s = tk * warp_sum<R>(M::acc_get(a));
+      typename M::acc_t a[3];
+#pragma unroll
+      for (int g = 0; g < 3; ++g) {
+        M::acc_init(a[g]);
+        if (on[g] && lane == 0) M::mac(a[g], M::one(), vv[g][k]);
+      }
+      for (int i = k + 1 + lane; i < n; i += PEPS_WARP) {
+        const R c = ck[i];
+#pragma unroll
+        for (int g = 0; g < 3; ++g)
+          if (on[g]) M::mac(a[g], c, vv[g][i]);
+      }
+      R sg3[3];
+#pragma unroll
+      for (int g = 0; g < 3; ++g) sg3[g] = M::acc_get(a[g]);
+#pragma unroll
+      for (int o = PEPS_WARP / 2; o > 0; o >>= 1) {
+#pragma unroll
+        for (int g = 0; g < 3; ++g) sg3[g] = sg3[g] + shfl_xor_r(sg3[g], o);
+      }
+#pragma unroll
+      for (int g = 0; g < 3; ++g) sg3[g] = tk * sg3[g];
       __syncwarp();
-      if (lane == 0) v[k] = v[k] - s;
-      for (int i = k + 1 + lane; i < n; i += PEPS_WARP) v[i] = v[i] - ck[i] * s;
+      if (lane == 0) {
+#pragma unroll
+        for (int g = 0; g < 3; ++g)
+          if (on[g]) vv[g][k] = vv[g][k] - sg3[g];
+      }
+      for (int i = k + 1 + lane; i < n; i += PEPS_WARP) {
+        const R c = ck[i];
+#pragma unroll
+        for (int g = 0; g < 3; ++g)
+          if (on[g]) vv[g][i] = M::sub_mul(vv[g][i], c, sg3[g]);
+      }
       __syncwarp();
     }
   }
