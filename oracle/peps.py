@@ -24,6 +24,8 @@ Readings taken where the paper is silent:
 """
 import numpy as np
 
+from . import flops as _f
+
 __all__ = [
     "bond_list", "site_tensor", "BMPS", "compress", "upper_envs", "lower_envs",
     "Strip1", "Strip2", "evaluate", "evaluate_batch", "gradient", "go_step",
@@ -96,9 +98,9 @@ def absorb(env, Trow, from_above):
         a, _, b = M.shape
         l, r, u, d = T.shape
         if from_above:
-            N = np.einsum("aub,lrud->aldbr", M, T).reshape(a * l, d, b * r)
+            N = _f.einsum("aub,lrud->aldbr", M, T).reshape(a * l, d, b * r)
         else:
-            N = np.einsum("adb,lrud->alubr", M, T).reshape(a * l, u, b * r)
+            N = _f.einsum("adb,lrud->alubr", M, T).reshape(a * l, u, b * r)
         out.append(N)
     return BMPS(out, env.logscale)
 
@@ -107,21 +109,22 @@ def compress(env, chi):
     """Truncate the bond dimension to chi: a left-to-right QR sweep brings the
     MPS to left-canonical form, then a right-to-left SVD sweep keeps the
     min(chi, m, n) largest singular values at each bond (Fig. 1(c)).  QR and
-    SVD are LAPACK's (numpy.linalg)."""
+    SVD are LAPACK's (numpy.linalg), called through the operation counter of
+    ``oracle.flops``."""
     sites = [x.copy() for x in env.sites]
     L = len(sites)
     for j in range(L - 1):
         a, p, b = sites[j].shape
-        Q, R = np.linalg.qr(sites[j].reshape(a * p, b), mode="reduced")
+        Q, R = _f.qr(sites[j].reshape(a * p, b))
         k = Q.shape[1]
         sites[j] = Q.reshape(a, p, k)
-        sites[j + 1] = np.einsum("kb,bpc->kpc", R, sites[j + 1])
+        sites[j + 1] = _f.einsum("kb,bpc->kpc", R, sites[j + 1])
     for j in range(L - 1, 0, -1):
         a, p, b = sites[j].shape
-        U, S, Vt = np.linalg.svd(sites[j].reshape(a, p * b), full_matrices=False)
+        U, S, Vt = _f.svd(sites[j].reshape(a, p * b), keep=min(chi, a, p * b))
         k = min(chi, S.shape[0])
         sites[j] = Vt[:k].reshape(k, p, b)
-        sites[j - 1] = np.einsum("apb,bk->apk", sites[j - 1], U[:, :k] * S[:k])
+        sites[j - 1] = _f.einsum("apb,bk->apk", sites[j - 1], U[:, :k] * S[:k])
     logscale = env.logscale
     for j in range(L):
         s = np.abs(sites[j]).max()
@@ -160,32 +163,32 @@ def lower_envs(A, spins, L, chi):
 # Column steps of the strips, written as pairwise tensordot contractions.
 def _left1(L, U, T, Dn):
     """L'[B,r,D] = sum L[x,y,z] U[x,u,B] T[y,r,u,d] Dn[z,d,D]."""
-    t = np.tensordot(L, U, axes=([0], [0]))          # y z u B
-    t = np.tensordot(t, T, axes=([0, 2], [0, 2]))    # z B r d
-    return np.tensordot(t, Dn, axes=([0, 3], [0, 1]))  # B r D
+    t = _f.tensordot(L, U, axes=([0], [0]))          # y z u B
+    t = _f.tensordot(t, T, axes=([0, 2], [0, 2]))    # z B r d
+    return _f.tensordot(t, Dn, axes=([0, 3], [0, 1]))  # B r D
 
 
 def _right1(U, T, Dn, R):
     """R'[x,y,z] = sum U[x,u,B] T[y,r,u,d] Dn[z,d,D] R[B,r,D]."""
-    t = np.tensordot(Dn, R, axes=([2], [2]))         # z d B r
-    t = np.tensordot(T, t, axes=([1, 3], [3, 1]))    # y u z B
-    return np.tensordot(U, t, axes=([1, 2], [1, 3])).transpose(0, 1, 2)  # x y z
+    t = _f.tensordot(Dn, R, axes=([2], [2]))         # z d B r
+    t = _f.tensordot(T, t, axes=([1, 3], [3, 1]))    # y u z B
+    return _f.tensordot(U, t, axes=([1, 2], [1, 3])).transpose(0, 1, 2)  # x y z
 
 
 def _left2(L, U, T1, T2, Dn):
     """L'[B,r,s,D] = sum L[w,x,y,z] U[w,u,B] T1[x,r,u,m] T2[y,s,m,d] Dn[z,d,D]."""
-    t = np.tensordot(L, U, axes=([0], [0]))          # x y z u B
-    t = np.tensordot(t, T1, axes=([0, 3], [0, 2]))   # y z B r m
-    t = np.tensordot(t, T2, axes=([0, 4], [0, 2]))   # z B r s d
-    return np.tensordot(t, Dn, axes=([0, 4], [0, 1]))  # B r s D
+    t = _f.tensordot(L, U, axes=([0], [0]))          # x y z u B
+    t = _f.tensordot(t, T1, axes=([0, 3], [0, 2]))   # y z B r m
+    t = _f.tensordot(t, T2, axes=([0, 4], [0, 2]))   # z B r s d
+    return _f.tensordot(t, Dn, axes=([0, 4], [0, 1]))  # B r s D
 
 
 def _right2(U, T1, T2, Dn, R):
     """R'[w,x,y,z] = sum U[w,u,B] T1[x,r,u,m] T2[y,s,m,d] Dn[z,d,D] R[B,r,s,D]."""
-    t = np.tensordot(Dn, R, axes=([2], [3]))         # z d B r s
-    t = np.tensordot(T2, t, axes=([1, 3], [4, 1]))   # y m z B r
-    t = np.tensordot(T1, t, axes=([1, 3], [4, 1]))   # x u y z B
-    return np.tensordot(U, t, axes=([1, 2], [1, 4]))  # w x y z
+    t = _f.tensordot(Dn, R, axes=([2], [3]))         # z d B r s
+    t = _f.tensordot(T2, t, axes=([1, 3], [4, 1]))   # y m z B r
+    t = _f.tensordot(T1, t, axes=([1, 3], [4, 1]))   # x u y z B
+    return _f.tensordot(U, t, axes=([1, 2], [1, 4]))  # w x y z
 
 
 def _unit(x):
@@ -234,7 +237,7 @@ class Strip1:
         x = self.Lenv[j]
         for k, T in enumerate(Ts):
             x = _left1(x, self.up.sites[j + k], T, self.dn.sites[j + k])
-        return float(np.einsum("xyz,xyz->", x, self.Renv[j + len(Ts)]))
+        return float(_f.einsum("xyz,xyz->", x, self.Renv[j + len(Ts)]))
 
     def ratio(self, j, new_T):
         """W_i(S')/W_i(S) where S' replaces the tensors of columns j, j+1...
@@ -246,9 +249,9 @@ class Strip1:
         """B^{s_m}(S) of Eq. delta for site (i, j), scaled so that dividing by
         ``scaled_value`` gives Delta: returns (B_scaled, W_scaled)."""
         # B = L_j U_j Dn_j R_{j+1} with the site tensor left out
-        lu = np.tensordot(self.Lenv[j], self.up.sites[j], axes=([0], [0]))   # y z u B
-        rd = np.tensordot(self.Renv[j + 1], self.dn.sites[j], axes=([2], [2]))  # B r z d
-        Bt = np.tensordot(lu, rd, axes=([1, 3], [2, 0]))                     # y u r d
+        lu = _f.tensordot(self.Lenv[j], self.up.sites[j], axes=([0], [0]))   # y z u B
+        rd = _f.tensordot(self.Renv[j + 1], self.dn.sites[j], axes=([2], [2]))  # B r z d
+        Bt = _f.tensordot(lu, rd, axes=([1, 3], [2, 0]))                     # y u r d
         Bt = Bt.transpose(0, 2, 1, 3)                                        # y r u d
         v = float(self.Lenv[self.L].reshape(()))
         # Bt carries exp(-(cL[j]+cR[j+1])), v carries exp(-cL[L])
@@ -283,7 +286,7 @@ class Strip2:
         x = self.Lenv[j]
         for k, (T1, T2) in enumerate(cols):
             x = self._step_left(x, j + k, T1, T2)
-        return float(np.einsum("wxyz,wxyz->", x, self.Renv[j + len(cols)]))
+        return float(_f.einsum("wxyz,wxyz->", x, self.Renv[j + len(cols)]))
 
     def ratio(self, j, new_cols):
         old = [(self.T1[j + k], self.T2[j + k]) for k in range(len(new_cols))]

@@ -25,6 +25,7 @@ import numpy as np
 
 from .peps import (BMPS, Strip1, Strip2, absorb, compress, lower_envs, row,
                    site_tensor)
+from .flops import tagged
 from .philox import philox4x32_10, uniform53
 
 __all__ = ["init_config", "metropolis_sweep", "sample_chains"]
@@ -49,7 +50,8 @@ def metropolis_sweep(A, spins, L, chi, seed, chain, sweep):
     """One sweep over all nearest-neighbour bonds; updates ``spins`` in place
     and returns the number of accepted exchanges."""
     key = (seed & 0xFFFFFFFF, seed >> 32)
-    dn = lower_envs(A, spins, L, chi)
+    with tagged("sweep_lower_envs"):
+        dn = lower_envs(A, spins, L, chi)
     up = BMPS.trivial(L)
     acc = 0
 
@@ -68,7 +70,8 @@ def metropolis_sweep(A, spins, L, chi, seed, chain, sweep):
             if uniform53(w[0], w[1]) < r * r:
                 spins[m1], spins[m2] = spins[m2], spins[m1]
                 acc += 1
-                strip = Strip1(A, spins, L, i, up, dn[i + 1])
+                with tagged("rebuild"):
+                    strip = Strip1(A, spins, L, i, up, dn[i + 1])
         if i < L - 1:
             strip2 = Strip2(A, spins, L, i, up, dn[i + 2])
             for j in range(L):
@@ -81,7 +84,8 @@ def metropolis_sweep(A, spins, L, chi, seed, chain, sweep):
                 if uniform53(w[0], w[1]) < r * r:
                     spins[m1], spins[m2] = spins[m2], spins[m1]
                     acc += 1
-                    strip2 = Strip2(A, spins, L, i, up, dn[i + 2])
+                    with tagged("rebuild"):
+                        strip2 = Strip2(A, spins, L, i, up, dn[i + 2])
             up = compress(absorb(up, row(A, spins, L, i), True), chi)
     return acc
 

@@ -276,9 +276,27 @@ def test_go_step_sign_update():
     for k in range(d.size):
         if gf[k] != 0:
             assert np.sign(d[k]) == -np.sign(gf[k]) and 0 < abs(d[k]) < dt
-            w = oracle.philox4x32_10((k, 0, 7, 2), (123, 0))
-            p = oracle.uniform_open53(w[0], w[1])
-            assert An.reshape(-1)[k] == A.reshape(-1)[k] - p * dt * np.sign(gf[k])
+
+
+def test_go_step_lengths_are_uniform_and_fresh_per_step():
+    """The step lengths p of the GO update (after Eq. delta) are i.i.d.
+    uniform on (0, 1): over 20000 elements their mean, quartiles and
+    lag-1 correlation match U(0,1) within 5 sigma, and another step number
+    draws other lengths."""
+    n = 20000
+    A = np.zeros((n, 1, 1, 1, 1, 1))
+    g = np.ones_like(A)
+    dt = 1.0
+    p = -(oracle.go_step(A, g, dt, seed=99, step=3) - A).reshape(-1)
+    assert p.min() > 0.0 and p.max() < 1.0
+    sig = np.sqrt(1.0 / 12.0 / n)
+    assert abs(p.mean() - 0.5) < 5 * sig
+    for q in (0.25, 0.5, 0.75):
+        assert abs(np.mean(p < q) - q) < 5 * np.sqrt(q * (1 - q) / n)
+    c = np.corrcoef(p[:-1], p[1:])[0, 1]
+    assert abs(c) < 5 / np.sqrt(n)
+    p2 = -(oracle.go_step(A, g, dt, seed=99, step=4) - A).reshape(-1)
+    assert abs(np.corrcoef(p, p2)[0, 1]) < 5 / np.sqrt(n)
 
 
 # --------------------------------------------------------------------------
@@ -289,6 +307,49 @@ def test_init_config_is_sz0_permutation():
         s = oracle.init_config(4, 99, c)
         assert s.sum() == 8 and s.dtype == np.uint8
     assert not np.array_equal(oracle.init_config(4, 99, 0), oracle.init_config(4, 99, 1))
+
+
+def test_init_config_is_uniform_over_the_sz0_sector():
+    """Fig. "contraction", Step 1 (a random start): the Fisher-Yates start
+    draws every S^z = 0 configuration with equal probability.  On the 2x2
+    lattice each of the C(4,2) = 6 configurations has probability 1/6 over
+    12000 chains, within 5 sigma (a shuffle that drew j from [0, k) instead
+    of [0, k] -- Sattolo's cycles -- never returns the start and fails); on
+    the 3x3 lattice every site is up with probability 4/9 over 6000 chains."""
+    from collections import Counter
+    n = 12000
+    cnt = Counter(tuple(oracle.init_config(2, 2024, c)) for c in range(n))
+    assert len(cnt) == 6
+    sig = np.sqrt((1 / 6) * (5 / 6) / n)
+    for k, v in cnt.items():
+        assert sum(k) == 2
+        assert abs(v / n - 1 / 6) < 5 * sig, (k, v)
+    n3 = 6000
+    S = np.array([oracle.init_config(3, 77, c) for c in range(n3)])
+    assert np.all(S.sum(axis=1) == 5)  # floor(9/2) = 4 up (s = 0), 5 down
+    up = np.mean(S == 0, axis=0)
+    assert np.all(np.abs(up - 4 / 9) < 5 * np.sqrt((4 / 9) * (5 / 9) / n3))
+
+
+def test_burn_in_and_thinning_record_the_stated_sweeps():
+    """sample_chains records the configuration after sweep t when t > n_burn
+    and (t - n_burn) % n_thin == 0: with n_burn = 2, n_thin = 3 and two
+    samples per chain that is after sweeps 5 and 8 (of 8), checked against
+    the chain advanced by hand, sweep by sweep."""
+    L, D, chi, seed = 3, 2, 4, 31337
+    A = make_peps(L, D, seed=8)
+    out, final, acc = oracle.sample_chains(A, L, chi, seed, 2, 2, 3, 2, first_sweep=11)
+    for c in range(2):
+        s = oracle.init_config(L, seed, c)
+        seen, a = {}, 0
+        for t in range(1, 9):
+            a += oracle.metropolis_sweep(A, s, L, chi, seed, c, 10 + t)
+            seen[t] = s.copy()
+        assert np.array_equal(out[2 * c], seen[5]) and np.array_equal(out[2 * c + 1], seen[8])
+        assert np.array_equal(final[c], seen[8]) and acc[c] == a
+    # the recorded sweeps differ from their neighbours for some chain (the
+    # rule is not vacuous on this input)
+    assert any(not np.array_equal(out[2 * c], out[2 * c + 1]) for c in range(2))
 
 
 def test_sampler_stationary_distribution_2x2():
