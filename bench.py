@@ -37,6 +37,14 @@ sys.path.insert(0, ROOT)
 from synth import CONFIGS, make_peps  # noqa: E402
 
 WORKLOAD = "16x16_D6_Dc24"
+FP64_MAX_WARMUP, FP64_MAX_STEPS = 2, 5
+
+# DRAM traffic of one launch of the fused kernel, bytes per chain (ncu
+# dram__bytes_read.sum + dram__bytes_write.sum over a smaller launch of the
+# same kernel, scaled by the chains it processed; the summaries under
+# profiles/ give the command).  Keyed by (workload, precision form); only
+# valid for the kernel the capture was taken from.
+TRAFFIC_PER_CHAIN = {}
 METRIC = "local-energy samples/s at 16x16 D=6 Dc=24, mixed vs FP64; p50/p99 latency"
 
 
@@ -139,12 +147,21 @@ def max_over_ranks(x, world):
 def cpu_baseline(cfg, A, n_samples, seed):
     """The FP64 oracle on a bounded sample of the workload on the host cores:
     n_samples configurations through one Metropolis sweep each and a full
-    evaluation (E, Delta), timed on the wall clock."""
+    evaluation (E, Delta), timed on the wall clock.  Returns (samples/s,
+    cores, oracle-counted flops per sample of the fused VMC step).
+
+    The flops are counted by the oracle's operation counter while it runs:
+    the evaluation plus the sweep, less the sweep's own rebuild of the lower
+    environments (the fused step reuses the evaluation's) and less the strip
+    rebuilds that follow an accepted exchange (an incremental sweep never
+    needs them)."""
     import oracle
+    from oracle import flops as oflops
     L, Dc = cfg["L"], cfg["Dc"]
     t0 = time.perf_counter()
-    out, _, _ = oracle.sample_chains(A, L, Dc, seed, n_samples, 0, 1, 1)
-    oracle.evaluate_batch(A, out, L, Dc, want_delta=True)
+    with oflops.counting() as cnt:
+        out, _, _ = oracle.sample_chains(A, L, Dc, seed, n_samples, 0, 1, 1)
+        oracle.evaluate_batch(A, out, L, Dc, want_delta=True)
     dt = time.perf_counter() - t0
     cores = os.cpu_count() or 1
     try:
@@ -153,7 +170,9 @@ def cpu_baseline(cfg, A, n_samples, seed):
         cores = max([i.get("num_threads", 1) for i in info] + [1])
     except Exception:
         pass
-    return n_samples / dt, cores
+    counted = cnt.by_class(exclude_tags=("rebuild", "sweep_lower_envs"))
+    flops = {k: v / n_samples for k, v in counted.items()}
+    return n_samples / dt, cores, flops
 
 
 def run_reference(args, cfg):
@@ -169,7 +188,7 @@ def run_reference(args, cfg):
     cores = 1
     for k in range(args.steps):
         t0 = time.perf_counter()
-        _, cores = cpu_baseline(cfg, A, per_step, 11 + k)
+        _, cores, _ = cpu_baseline(cfg, A, per_step, 11 + k)
         times.append(time.perf_counter() - t0)
     ms = 1e3 * float(np.mean(times))
     value = per_step / (ms / 1e3)
@@ -278,8 +297,8 @@ def main():
     full_batch = cfg.get("batch", cfg.get("chains", 256))
     B = args.batch or 2 * slots
     seed = 0x5EED0000 + cfg["seed"]
-    from paper_1806_03761_gb300.dist import allreduce_sums, shard
-    chain_offset, B = shard(rank, world, B * world)
+    from paper_1806_03761_gb300.dist import allreduce_sums, weak_scaling_plan
+    chain_offset, B, M_total = weak_scaling_plan(rank, world, B)
     stream = torch.cuda.current_stream()
     # chains start from their Fisher-Yates states; every step continues them
     state = ctx.sample(seed, B, 0, 1, 1, chain_offset=chain_offset, first_sweep=1)
@@ -301,7 +320,7 @@ def main():
         counters["step"] += 1
 
     for _ in range(args.warmup):
-        vmc_step(ctx, state, sums, out, B * world)
+        vmc_step(ctx, state, sums, out, M_total)
     torch.cuda.synchronize()
     barrier(world)
 
@@ -324,7 +343,7 @@ def main():
         k0.record(stream)
         state.copy_(host_state, non_blocking=True)        # H2D: chain states
         k1.record(stream)
-        vmc_step(ctx, state, sums, out, B * world)
+        vmc_step(ctx, state, sums, out, M_total)
         k2.record(stream)
         host_e.copy_(out["e_loc"], non_blocking=True)     # D2H: energies, sum E
         host_se.copy_(sums[2], non_blocking=True)
@@ -342,54 +361,82 @@ def main():
     dev_ms = max_over_ranks(float(np.sum(step_ms)), world) / max(args.steps, 1)
     e2e_total = max_over_ranks(t_start.elapsed_time(t_end), world) / max(args.steps, 1)
 
-    # the mixed form against the FP64 GPU path: one wave of chains, one step
+    # the mixed form against the FP64 GPU path: the same batch of chains and
+    # the same step, timed the same way (warm-up and timed steps capped at
+    # FP64_MAX_WARMUP / FP64_MAX_STEPS: an FP64 step takes about twice as long)
     fp64 = None
     if args.precision == "mixed" and not args.no_fp64_compare and world == 1:
         c64 = P.PepsContext(L, D, Dc, precision="fp64", slots=args.slots)
-        c64.set_tensors(A)
-        nb = min(B, c64.slots)
-        st64 = state[:nb].clone()
-        s64 = c64.new_sums()
-        o64 = dict(e_loc=torch.empty(nb, dtype=torch.float64, device="cuda"),
-                   log_abs=torch.empty(nb, dtype=torch.float64, device="cuda"),
-                   sign=torch.empty(nb, dtype=torch.int8, device="cuda"))
-        c64.vmc_step(seed, st64[:8].clone(), 1, sums=s64)  # warm-up launch
         A64 = A.clone()
+        c64.set_tensors(A64)
+        st64 = state.clone()
+        s64 = c64.new_sums()
+        o64 = dict(e_loc=torch.empty(B, dtype=torch.float64, device="cuda"),
+                   log_abs=torch.empty(B, dtype=torch.float64, device="cuda"),
+                   sign=torch.empty(B, dtype=torch.int8, device="cuda"))
+        cnt64 = {"sweep": counters["sweep"], "step": counters["step"]}
+
+        def step64():
+            c64.vmc_step(seed, st64, cnt64["sweep"], chain_offset=chain_offset, sums=s64, out=o64)
+            c64.grad_step(s64, M_total, args.dt, seed, cnt64["step"], A64)
+            cnt64["sweep"] += 1
+            cnt64["step"] += 1
+
+        w64, k64 = min(args.warmup, FP64_MAX_WARMUP), max(1, min(args.steps, FP64_MAX_STEPS))
+        for _ in range(w64):
+            step64()
         torch.cuda.synchronize()
-        a64, b64 = ev(), ev()
-        a64.record(stream)
-        c64.vmc_step(seed, st64, counters["sweep"], chain_offset=chain_offset, sums=s64, out=o64)
-        c64.grad_step(s64, nb, args.dt, seed, counters["step"], A64)
-        b64.record(stream)
-        torch.cuda.synchronize()
-        t64 = a64.elapsed_time(b64)
-        fp64 = {"value": nb / (t64 / 1e3), "unit": "samples/s", "batch": nb,
-                "ms_per_step": t64, "slots": c64.slots}
-        del c64
+        ms64 = []
+        for _ in range(k64):
+            a64, b64 = ev(), ev()
+            a64.record(stream)
+            step64()
+            b64.record(stream)
+            torch.cuda.synchronize()
+            ms64.append(a64.elapsed_time(b64))
+        rc64, fl64 = c64.sync_status()
+        t64 = float(np.mean(ms64))
+        fp64 = {"value": B / (t64 / 1e3), "unit": "samples/s", "batch": B,
+                "ms_per_step": t64, "steps": k64, "warmup": w64, "slots": c64.slots,
+                "p50_ms": float(np.percentile(ms64, 50)), "p99_ms": float(np.percentile(ms64, 99)),
+                "status": {"rc": rc64, "flags": fl64}}
+        c64.close()
 
     if rank != 0:
         return
-    value = B * world / (dev_ms / 1e3)
-    # roofline of the dominant kernel: the fused evaluation + sweep kernel
-    # (the per-slot reduction inside the same bracket is < 0.1 % of it)
-    flops = P.flops_per_sample(L, D, Dc, precision=args.precision, what="vmc")
-    achieved = flops * B / (float(np.mean(step_ms)) / 1e3) / 1e12
-    sm_max = clk.get("sm_max_mhz") or 2070.0
-    if args.precision == "fp64":
-        peak, unit = 152 * 2 * 2 * sm_max * 1e6 / 1e12, "TFLOP/s (FP64 pipe: 2 DFMA/clk/SM)"
-    elif args.precision == "mixed":
-        # float-float multiply-add = 12 FP32 instructions on 128 lanes per SM
-        peak, unit = 152 * 128 * 2 * sm_max * 1e6 / 12 / 1e12, "TFLOP/s (FP32 pipe / 12 per ff MAC)"
-    else:
-        peak, unit = 152 * 128 * 2 * sm_max * 1e6 / 1e12, "TFLOP/s (FP32 pipe)"
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": unit,
-            "frac": achieved / peak, "traffic": None, "kernel": "peps_vmc_kernel",
-            "flops_per_sample": flops, "peak_source": "unit counts x sampled max SM clock"}
-    cpu = None
+    value = M_total / (dev_ms / 1e3)
+    cpu, oflops = None, None
     if not args.no_cpu_baseline and world == 1:
-        v, cores = cpu_baseline(cfg, A_host, 1, 99)
+        v, cores, oflops = cpu_baseline(cfg, A_host, 1, 99)
         cpu = {"value": v, "unit": "samples/s", "cores": cores, "kind": "oracle",
                "sample": "1 chain x 1 Metropolis sweep + full evaluation (E, Delta)"}
+    # roofline of the dominant kernel, the fused evaluation + sweep kernel (the
+    # per-slot reduction and the GO update inside the bracket are < 0.1 % of it).
+    # Numerator: the oracle's operation count of one fused step per chain,
+    # counted live above (falls back to the kernels' own model without it).
+    model_flops = P.flops_per_sample(L, D, Dc, precision=args.precision, what="vmc")
+    flops = sum(oflops.values()) if oflops else model_flops
+    sec = float(np.mean(step_ms)) / 1e3
+    achieved = flops * B / sec / 1e12
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    if args.precision == "fp64":
+        peak, unit = sms * 2 * 2 * sm_max * 1e6 / 1e12, "TFLOP/s (FP64 pipe: 2 DFMA/clk/SM)"
+    elif args.precision == "mixed":
+        # float-float multiply-add = 12 FP32 instructions on 128 lanes per SM
+        peak, unit = sms * 128 * 2 * sm_max * 1e6 / 12 / 1e12, "TFLOP/s (FP32 pipe / 12 per ff MAC)"
+    else:
+        peak, unit = sms * 128 * 2 * sm_max * 1e6 / 1e12, "TFLOP/s (FP32 pipe)"
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": achieved / peak, "traffic": (TRAFFIC_PER_CHAIN[(args.workload, args.precision)] * B
+                        if (args.workload, args.precision) in TRAFFIC_PER_CHAIN else None),
+            "kernel": "peps_vmc_kernel",
+            "flops_per_sample": flops,
+            "flops_source": "oracle operation counter (1 chain)" if oflops else "kernel model",
+            "flops_per_sample_by_class": oflops,
+            "flops_per_sample_kernel_model": model_flops,
+            "frac_kernel_model": model_flops * B / sec / 1e12 / peak,
+            "peak_source": "unit counts x %d SMs (device) x sampled max SM clock" % sms}
     lat = sorted(step_ms)
     h2d, d2h = B * N, B * N + B * 8 + 8
     metric = METRIC if args.workload == WORKLOAD else \
@@ -408,7 +455,7 @@ def main():
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "latency_per": "batch (one step)",
             "roofline": roof, "cpu_baseline": cpu,
-            "e2e": {"value": B * world / (e2e_total / 1e3), "unit": "samples/s",
+            "e2e": {"value": M_total / (e2e_total / 1e3), "unit": "samples/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": e2e_total, "copy_ms_per_step": float(np.mean(e2e_ms) - np.mean(step_ms))},
             "fp64_gpu": fp64,

@@ -15,6 +15,16 @@ def shard(rank, world, chains_per_rank):
     return rank * chains_per_rank, chains_per_rank
 
 
+def weak_scaling_plan(rank, world, chains_per_rank):
+    """The weak-scaling layout of a VMC step: every rank keeps the same
+    number of chains B as the world grows.  Returns (chain offset of this
+    rank, chains of this rank, M) with M = B * world the number of samples
+    the all-reduced gradient sums cover (the Monte Carlo mean of Eq.
+    gradients divides by M)."""
+    off, n = shard(rank, world, chains_per_rank)
+    return off, n, chains_per_rank * world
+
+
 def allreduce_sums(sums, world):
     """Sum the gradient accumulators over ranks in place (no-op for one rank)."""
     if world == 1:

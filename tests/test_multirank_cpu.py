@@ -24,10 +24,10 @@ def _free_port():
 
 def _rank_sums(rank, world):
     import oracle
-    from paper_1806_03761_gb300.dist import shard
+    from paper_1806_03761_gb300.dist import weak_scaling_plan
     from synth import make_peps
     A = make_peps(L, D, seed=5)
-    off, n = shard(rank, world, CHAINS)
+    off, n, _ = weak_scaling_plan(rank, world, CHAINS)
     out, _, _ = oracle.sample_chains(A, L, DC, SEED, n, 2, 1, 1, chain_offset=off)
     r = oracle.evaluate_batch(A, out, L, DC, want_delta=True)
     sd = np.zeros((L * L, 2, D ** 4))
@@ -45,10 +45,11 @@ def _worker(rank, world, port, q):
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     import oracle
-    from paper_1806_03761_gb300.dist import allreduce_sums
+    from paper_1806_03761_gb300.dist import allreduce_sums, weak_scaling_plan
     A, sums = _rank_sums(rank, world)
     allreduce_sums(sums, world)
-    g = oracle.gradient(sums[0].numpy(), sums[1].numpy(), float(sums[2][0]), CHAINS * world)
+    _, _, M = weak_scaling_plan(rank, world, CHAINS)
+    g = oracle.gradient(sums[0].numpy(), sums[1].numpy(), float(sums[2][0]), M)
     An = oracle.go_step(A, g.reshape(A.shape), 0.01, SEED, 3)
     q.put((rank, An, sums[2].item()))
     dist.destroy_process_group()
@@ -83,3 +84,18 @@ def test_shard_bounds():
     assert shard(0, 4, 10) == (0, 10) and shard(3, 4, 10) == (30, 10)
     with pytest.raises(ValueError):
         shard(4, 4, 10)
+
+
+def test_weak_scaling_plan_keeps_the_per_rank_batch():
+    """The bench's layout for world = 1, 2, 8: every rank runs B chains, the
+    ranks' chain ranges are disjoint and together cover 0 .. B*world-1, and the
+    gradient mean divides by M = B * world (the chains actually summed)."""
+    from paper_1806_03761_gb300.dist import weak_scaling_plan
+    B = 608
+    for world in (1, 2, 8):
+        seen = []
+        for rank in range(world):
+            off, n, M = weak_scaling_plan(rank, world, B)
+            assert n == B and M == B * world
+            seen.extend(range(off, off + n))
+        assert sorted(seen) == list(range(B * world))
