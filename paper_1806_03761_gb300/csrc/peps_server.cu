@@ -70,16 +70,23 @@ struct peps_server {
   size_t budget = 0;
   size_t active_bytes = 0, idle_bytes = 0;
   int64_t next_id = 1;
-  bool stop = false;
+  bool stop = false, reap_stop = false;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<Job*> pending;
   std::vector<Job*> active;
   std::map<int64_t, Job*> jobs;
   std::vector<IdleCtx> idle;  // least recently used first
-  std::thread worker;
+  // evicted contexts on their way out: freed by the reaper thread, so that
+  // cudaFree (which waits for the whole device) never stalls the worker;
+  // their bytes stay reserved until the memory is back
+  std::deque<IdleCtx> reap;
+  size_t reaping_bytes = 0;
+  std::condition_variable cv_reap;
+  std::thread worker, reaper;
 
   void run();
+  void reap_loop();
   bool admit(Job* j);
   void finish(Job* j, int status);
   void release(Job* j);
@@ -137,16 +144,17 @@ bool peps_server::admit(Job* j) {
   return true;
 }
 
-// Free a job's per-job device state (stream-ordered, no device-wide wait) and
-// return its context to the pool.
+// Free a job's per-job device state and return its context to the pool.
+// Nothing here waits: the frees are stream-ordered (they take effect when the
+// job's stream reaches them) and cudaStreamDestroy returns at once, the
+// stream's resources being released when its work is done.
 void peps_server::release(Job* j) {
   if (j->stream) {
-    cudaFreeAsync(j->dA, j->stream);
-    cudaFreeAsync(j->dspins, j->stream);
-    cudaFreeAsync(j->de, j->stream);
-    cudaFreeAsync(j->dla, j->stream);
-    cudaFreeAsync(j->dsg, j->stream);
-    cudaStreamSynchronize(j->stream);
+    if (j->dA) cudaFreeAsync(j->dA, j->stream);
+    if (j->dspins) cudaFreeAsync(j->dspins, j->stream);
+    if (j->de) cudaFreeAsync(j->de, j->stream);
+    if (j->dla) cudaFreeAsync(j->dla, j->stream);
+    if (j->dsg) cudaFreeAsync(j->dsg, j->stream);
     cudaStreamDestroy(j->stream);
   }
   if (j->ev) cudaEventDestroy(j->ev);
@@ -175,7 +183,7 @@ void peps_server::run() {
   cudaSetDevice(device);
   for (;;) {
     std::vector<Job*> admitted;
-    std::vector<peps_ctx*> evict;
+    int evicted = 0;
     {
       std::unique_lock<std::mutex> lock(mu);
       // admission in arrival order while the budget allows
@@ -189,14 +197,19 @@ void peps_server::run() {
         // evict idle contexts (least recently used first) while they stand
         // between this job and the budget
         size_t freeable = idle_bytes - (reuse >= 0 ? idle[reuse].bytes : 0);
-        if (active_bytes + idle_bytes + need > budget + freeable) break;
-        for (int q = 0; active_bytes + idle_bytes + need > budget && q < (int)idle.size();) {
+        if (active_bytes + idle_bytes + reaping_bytes + need > budget + freeable) break;
+        for (int q = 0; active_bytes + idle_bytes + reaping_bytes + need > budget && q < (int)idle.size();) {
           if (q == reuse) { ++q; continue; }
-          evict.push_back(idle[q].ctx);
+          reap.push_back(idle[q]);
+          reaping_bytes += idle[q].bytes;
           idle_bytes -= idle[q].bytes;
           idle.erase(idle.begin() + q);
           if (reuse > q) --reuse;
+          ++evicted;
         }
+        // the evicted memory is not back yet: admit once the reaper has
+        // freed enough of it (the other jobs keep running meanwhile)
+        if (active_bytes + idle_bytes + reaping_bytes + need > budget) break;
         if (reuse >= 0) {
           j->ctx = idle[reuse].ctx;
           idle_bytes -= idle[reuse].bytes;
@@ -208,7 +221,7 @@ void peps_server::run() {
       }
       if (stop && pending.empty() && active.empty() && admitted.empty()) break;
     }
-    for (peps_ctx* c : evict) peps_destroy(c);
+    if (evicted) cv_reap.notify_one();
     for (Job* j : admitted)
       if (admit(j)) active.push_back(j);
     // progress: one wave in flight per job
@@ -253,9 +266,32 @@ void peps_server::run() {
     }
     if (!progressed) {
       std::unique_lock<std::mutex> lock(mu);
-      if (pending.empty() || !active.empty())
+      if (pending.empty() || !active.empty() || reaping_bytes > 0)
         cv_work.wait_for(lock, std::chrono::microseconds(200));
     }
+  }
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    reap_stop = true;
+  }
+  cv_reap.notify_one();
+}
+
+// The reaper: destroys evicted contexts (peps_destroy -> cudaFree) off the
+// worker thread and hands their bytes back to the budget.
+void peps_server::reap_loop() {
+  cudaSetDevice(device);
+  std::unique_lock<std::mutex> lock(mu);
+  for (;;) {
+    cv_reap.wait(lock, [this] { return !reap.empty() || reap_stop; });
+    if (reap.empty()) break;
+    IdleCtx c = reap.front();
+    reap.pop_front();
+    lock.unlock();
+    peps_destroy(c.ctx);
+    lock.lock();
+    reaping_bytes -= c.bytes;
+    cv_work.notify_one();
   }
 }
 
@@ -274,6 +310,7 @@ int peps_server_create(size_t hbm_budget_bytes, int32_t slots_per_job, peps_serv
   s->device = dev;
   s->default_slots = slots_per_job > 0 ? slots_per_job : 2 * sms;
   s->budget = hbm_budget_bytes > 0 ? hbm_budget_bytes : (size_t)(0.9 * (double)fr);
+  s->reaper = std::thread([s] { s->reap_loop(); });
   s->worker = std::thread([s] { s->run(); });
   *out = s;
   return PEPS_OK;
@@ -338,6 +375,7 @@ int peps_server_destroy(peps_server* s) {
   }
   s->cv_work.notify_all();
   if (s->worker.joinable()) s->worker.join();
+  if (s->reaper.joinable()) s->reaper.join();
   cudaSetDevice(s->device);
   for (IdleCtx& c : s->idle) peps_destroy(c.ctx);
   for (auto& kv : s->jobs) delete kv.second;

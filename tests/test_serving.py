@@ -112,3 +112,48 @@ def test_invalid_jobs_refused(server_mod):
     with pytest.raises(P.PepsError):
         srv.submit(A, S[:0], 4, 2, 4, "fp64")  # empty batch
     srv.close()
+
+
+@pytest.mark.gpu
+def test_a_job_arriving_later_overlaps_a_running_one(server_mod):
+    """Continuous batching: under an ample budget a short job submitted while
+    a long one runs is admitted and finished before the long one is done,
+    and its result is the one it has alone."""
+    P = server_mod
+    long_job = (8, 4, 16, "mixed", 64, 21, "neel")  # 16 waves of 4 slots
+    short_job = (4, 2, 4, "fp64", 4, 22, "gauss")   # one wave
+    (Al, Sl), (As, Ss) = _inputs(long_job), _inputs(short_job)
+    srv = P.PepsServer(slots_per_job=4)
+    alone = srv.wait(srv.submit(As, Ss, *short_job[:4]))
+    i_long = srv.submit(Al, Sl, *long_job[:4])
+    i_short = srv.submit(As, Ss, *short_job[:4])
+    r_short = srv.wait(i_short)
+    r_long = srv.wait(i_long)
+    srv.close()
+    assert r_long["status"] == 0 and r_short["status"] == 0
+    assert r_short["admit_s"] < r_long["done_s"]
+    assert r_short["done_s"] < r_long["done_s"]
+    assert np.array_equal(r_short["e_loc"], alone["e_loc"])
+    assert np.array_equal(r_short["sign"], alone["sign"])
+
+
+@pytest.mark.gpu
+def test_eviction_under_a_tight_budget_keeps_results(server_mod):
+    """Idle contexts are evicted (freed off the worker thread) when a new
+    shape needs their memory; every job still returns its alone result."""
+    P = server_mod
+    jobs = [JOBS[0], JOBS[2], JOBS[0], JOBS[2]]
+    inputs = [_inputs(j) for j in jobs]
+    probe = P.PepsServer(slots_per_job=8)
+    alone = [probe.wait(probe.submit(A, S, *j[:4])) for j, (A, S) in zip(jobs, inputs)]
+    fps = [a["footprint_bytes"] for a in alone]
+    probe.close()
+    # room for one job's context and buffers at a time: every shape change
+    # evicts the other shape's idle context
+    srv = P.PepsServer(hbm_budget_bytes=int(1.2 * max(fps)), slots_per_job=8)
+    ids = [srv.submit(A, S, *j[:4]) for j, (A, S) in zip(jobs, inputs)]
+    res = [srv.wait(i) for i in ids]
+    srv.close()
+    for a, r in zip(alone, res):
+        assert r["status"] == 0
+        assert np.array_equal(a["e_loc"], r["e_loc"])
