@@ -200,7 +200,10 @@ int peps_sample_batch(peps_ctx* ctx, uint64_t seed, int64_t n_chains,
  * when fewer samples fit than the GPU could run, they run fewer at a
  * time.  Calls no allocating routine.  The first call on a device looks up
  * the array's device address (cudaGetSymbolAddress) with that device current:
- * make that first call before any stream capture.  Every call reuses the
+ * make that first call before any stream capture.  The address is kept with
+ * the id of the device's context and looked up again when the context has
+ * changed (after cudaDeviceReset the next call is again a first call).  Every
+ * call reuses the
  * same array, so calls that overlap on the GPU (other streams, other host
  * threads) race: order them.  Device-side conditions (zero amplitude,
  * non-finite input) are only reflected in sign = 0 / log_abs. */

@@ -63,75 +63,11 @@ cudaError_t launch_vmc_form(const EvalArgs<double>& a, const SampleArgs<double>&
 cudaError_t launch_vmc_form(const EvalArgs<ff>& a, const SampleArgs<ff>& b, int g, cudaStream_t s) { return peps_launch_vmc_ff(a, b, g, s); }
 cudaError_t launch_vmc_form(const EvalArgs<float>& a, const SampleArgs<float>& b, int g, cudaStream_t s) { return peps_launch_vmc_f32(a, b, g, s); }
 
-int64_t up32(int64_t x) { return (x + 31) & ~int64_t(31); }
-
-// Bond dimensions of every absorption step (see peps_plan.h).
+// Bond dimensions of every absorption step and the slot layout (peps_plan.h).
 void make_plan(const peps_shape& s, int nslots, PepsPlan* P, std::vector<PepsStep>* steps) {
-  const int L = s.L, D = s.D, Dc = s.Dc;
-  std::memset(P, 0, sizeof(*P));
-  P->L = L; P->D = D; P->Dc = Dc; P->N = L * L;
-  P->D2 = D * D; P->D3 = D * D * D; P->D4 = D * D * D * D;
-  P->nbonds = 2 * L * (L - 1) + 2 * (L - 1) * (L - 1);
-  P->J1 = s.J1; P->J2 = s.J2;
-  P->nsteps = L - 1;
-  steps->assign(L - 1, PepsStep());
-  for (int t = 0; t < L - 1; ++t) {
-    PepsStep& st = (*steps)[t];
-    std::memset(&st, 0, sizeof(st));
-    for (int j = 0; j < L; ++j) {
-      if (t == 0) { st.ia[j] = 1; st.ip[j] = 1; st.ib[j] = 1; }
-      else { st.ia[j] = (*steps)[t - 1].oa[j]; st.ip[j] = D; st.ib[j] = (*steps)[t - 1].ob[j]; }
-    }
-    const int Q = D;
-    int rprev = 1;
-    for (int j = 0; j < L - 1; ++j) {
-      int Bj = st.ib[j] * ((j == L - 1) ? 1 : D);
-      int r = std::min(rprev * Q, Bj);
-      st.r[j] = (int16_t)r;
-      rprev = r;
-    }
-    int cn = 1;
-    for (int j = L - 1; j >= 1; --j) {
-      int k = std::min(Dc, std::min((int)st.r[j - 1], Q * cn));
-      st.oa[j] = (int16_t)k;
-      st.ob[j] = (int16_t)cn;
-      cn = k;
-    }
-    st.oa[0] = 1;
-    st.ob[0] = (int16_t)cn;
-  }
-  P->site_cap = (int64_t)Dc * D * Dc;
-  P->env_cap = (int64_t)L * P->site_cap;
-  P->big_cap = (int64_t)Dc * Dc * D * D * D;
-  P->mat_cap = (int64_t)(Dc * D) * (Dc * D);
-  P->env2_cap = (int64_t)Dc * D * D * Dc;
-  int64_t o = 0;
-  auto take = [&](int64_t n) { int64_t r = o; o += up32(n); return r; };
-  P->off_dn = take((int64_t)(L + 1) * P->env_cap);
-  P->off_up = take(3 * P->env_cap);
-  P->off_rst = take((int64_t)L * P->mat_cap);
-  P->off_b0 = take(P->big_cap);
-  P->off_b1 = take(P->big_cap);
-  P->off_b2 = take(P->big_cap);
-  P->off_y = take(P->mat_cap);
-  P->off_xj = take(P->mat_cap);
-  P->off_vt = take(std::max<int64_t>(P->site_cap, P->D4));
-  P->off_c0 = take(P->site_cap);
-  P->off_c1 = take(P->site_cap);
-  P->off_l1 = take((int64_t)(L + 1) * P->site_cap);
-  P->off_r1 = take((int64_t)(L + 1) * P->site_cap);
-  P->off_l2 = take((int64_t)(L + 1) * P->env2_cap);
-  P->off_r2 = take((int64_t)(L + 1) * P->env2_cap);
-  P->off_alpha = take(3 * (int64_t)Dc * D + 16);
-  P->off_inv = take(13 * (int64_t)Dc * Dc * D);
-  P->off_tmp = take(32);
-  P->slot_elems = o;
-  int64_t d = 0;
-  auto taked = [&](int64_t n) { int64_t r = d; d += up32(n); return r; };
-  P->doff_scale = taked(4 * (L + 1));
-  P->doff_delta = taked((int64_t)P->N * P->D4);
-  P->doff_alpha = taked((int64_t)Dc * D + 8);
-  P->slot_doubles = d;
+  steps->assign(s.L - 1, PepsStep());
+  peps_plan_steps(s.L, s.D, s.Dc, s.J1, s.J2, P, steps->data());
+  peps_plan_layout(P, false);
   (void)nslots;
 }
 
@@ -555,7 +491,7 @@ double peps_flops_per_sample(const peps_shape* shape, int32_t what) {
       sweep_strips += 2 * step1;                                       // right env + left advance
       if (j + 1 < L) {
         eval_strips += 0.5 * 2 * step1;                                // horizontal ratio (2 steps)
-        sweep_strips += 0.5 * 4 * step1;                               // num + den (4 steps)
+        sweep_strips += 0.5 * 3 * step1;  // num (2 steps) + den (2, the first is the left advance)
       }
       if (i + 1 < L) {
         double pd2 = i + 1 == L - 1 ? 1 : D;
@@ -564,7 +500,7 @@ double peps_flops_per_sample(const peps_shape* shape, int32_t what) {
                     2 * ad2 * bu * Dr * Dr * pd2 * Dl * D + 2 * bu * Dr * Dr * bd2 * ad2 * pd2;
         eval_strips += 2 * s2;                                         // left + right envs
         eval_strips += 0.5 * s2 + (j + 1 < L ? 0.5 * 2 * 2 * s2 : 0);  // v, d, a ratios
-        sweep_strips += 2 * s2 + 0.5 * 2 * s2;                         // envs + vertical num/den
+        sweep_strips += 2 * s2 + 0.5 * s2;  // right env, left advance (= den), num
       }
     }
   }

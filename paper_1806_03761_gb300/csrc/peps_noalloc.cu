@@ -78,88 +78,63 @@ __global__ void __launch_bounds__(PEPS_NT, PEPS_MINB) peps_amp_noalloc_kernel(Ev
   }
 }
 
-int64_t up32(int64_t x) { return (x + 31) & ~int64_t(31); }
-
-// The bond dimensions and the per-slot workspace layout of the FP64 form
-// (the same recurrences as the context's plan).
+// The bond dimensions and the amplitude-only slot layout of the FP64 form:
+// the context's plan (peps_plan.h) without the two-row strip environments
+// and the Delta staging, which this entry point never touches.
 void plan_fp64(const peps_shape& s, PepsPlan* P, NoallocSteps* steps) {
-  const int L = s.L, D = s.D, Dc = s.Dc;
-  std::memset(P, 0, sizeof(*P));
   std::memset(steps, 0, sizeof(*steps));
-  P->L = L; P->D = D; P->Dc = Dc; P->N = L * L;
-  P->D2 = D * D; P->D3 = D * D * D; P->D4 = D * D * D * D;
-  P->nbonds = 2 * L * (L - 1) + 2 * (L - 1) * (L - 1);
-  P->J1 = s.J1; P->J2 = s.J2;
-  P->nsteps = L - 1;
-  for (int t = 0; t < L - 1; ++t) {
-    PepsStep& st = steps->s[t];
-    for (int j = 0; j < L; ++j) {
-      if (t == 0) { st.ia[j] = 1; st.ip[j] = 1; st.ib[j] = 1; }
-      else { st.ia[j] = steps->s[t - 1].oa[j]; st.ip[j] = D; st.ib[j] = steps->s[t - 1].ob[j]; }
-    }
-    int rprev = 1;
-    for (int j = 0; j < L - 1; ++j) {
-      int r = std::min(rprev * D, st.ib[j] * D);
-      st.r[j] = (int16_t)r;
-      rprev = r;
-    }
-    int cn = 1;
-    for (int j = L - 1; j >= 1; --j) {
-      int k = std::min(Dc, std::min((int)st.r[j - 1], D * cn));
-      st.oa[j] = (int16_t)k;
-      st.ob[j] = (int16_t)cn;
-      cn = k;
-    }
-    st.oa[0] = 1;
-    st.ob[0] = (int16_t)cn;
-  }
-  P->site_cap = (int64_t)Dc * D * Dc;
-  P->env_cap = (int64_t)L * P->site_cap;
-  P->big_cap = (int64_t)Dc * Dc * D * D * D;
-  P->mat_cap = (int64_t)(Dc * D) * (Dc * D);
-  P->env2_cap = (int64_t)Dc * D * D * Dc;
-  int64_t o = 0;
-  auto take = [&](int64_t n) { int64_t r = o; o += up32(n); return r; };
-  P->off_dn = take((int64_t)(L + 1) * P->env_cap);
-  P->off_up = take(3 * P->env_cap);
-  P->off_rst = take((int64_t)L * P->mat_cap);
-  P->off_b0 = take(P->big_cap);
-  P->off_b1 = take(P->big_cap);
-  P->off_b2 = take(P->big_cap);
-  P->off_y = take(P->mat_cap);
-  P->off_xj = take(P->mat_cap);
-  P->off_vt = take(std::max<int64_t>(P->site_cap, P->D4));
-  P->off_c0 = take(P->site_cap);
-  P->off_c1 = take(P->site_cap);
-  P->off_l1 = take((int64_t)(L + 1) * P->site_cap);
-  P->off_r1 = take((int64_t)(L + 1) * P->site_cap);
-  P->off_l2 = 0;  // the two-row strip is not used by this entry point
-  P->off_r2 = 0;
-  P->off_alpha = take(3 * (int64_t)Dc * D + 16);
-  P->off_inv = take(13 * (int64_t)Dc * Dc * D);
-  P->off_tmp = take(32);
-  P->slot_elems = o;
-  int64_t d = 0;
-  auto taked = [&](int64_t n) { int64_t r = d; d += up32(n); return r; };
-  P->doff_scale = taked(4 * (L + 1));
-  P->doff_delta = 0;
-  P->doff_alpha = 0;
-  P->slot_doubles = d;
+  peps_plan_steps(s.L, s.D, s.Dc, s.J1, s.J2, P, steps->s);
+  peps_plan_layout(P, true);
 }
 
-// Device address of the scratch array, looked up once per device with that
-// device current (the array's name is only a host-side stand-in).
+// Device address of the scratch array, looked up with the device current
+// (the array's name is only a host-side stand-in).  The address belongs to the
+// device's current context: it is cached together with that context's id and
+// looked up again when the id changes (cudaDeviceReset ends the primary
+// context, and the next call on the device runs in a new one).  The driver's
+// context calls are reached through the runtime's entry-point query, so the
+// library does not link against the driver library.
+typedef int (*CtxGetCurrentFn)(void**);
+typedef int (*CtxGetIdFn)(void*, unsigned long long*);
+
 std::mutex g_mu;
 void* g_addr[64] = {nullptr};
+unsigned long long g_ctx_id[64] = {0};
+
+bool current_context_id(unsigned long long* id) {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    cudaDriverEntryPointQueryResult q1, q2;
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) ==
+            cudaSuccess && q1 == cudaDriverEntryPointSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) ==
+            cudaSuccess && q2 == cudaDriverEntryPointSuccess) {
+      get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+      get_id = reinterpret_cast<CtxGetIdFn>(f2);
+    }
+  }
+  void* ctx = nullptr;
+  if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx) return false;
+  return get_id(ctx, id) == 0;
+}
 
 cudaError_t scratch_address(int dev, void** out) {
   std::lock_guard<std::mutex> lock(g_mu);
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-  if (!g_addr[dev]) {
+  unsigned long long id = 0;
+  const bool have_id = current_context_id(&id);
+  if (!g_addr[dev] || !have_id || id != g_ctx_id[dev]) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, peps_noalloc_scratch);
     if (e != cudaSuccess) return e;
     g_addr[dev] = p;
+    // the id is read again: the lookup above may have created the context
+    if (have_id || current_context_id(&id)) g_ctx_id[dev] = id;
   }
   *out = g_addr[dev];
   return cudaSuccess;

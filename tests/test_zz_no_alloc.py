@@ -66,3 +66,24 @@ def test_noalloc_rejects_shapes_beyond_its_scratch(lib):
     mixed = _lib.PepsShape(4, 2, 4, 1.0, 0.5, _lib.PEPS_MIXED)
     rc, _, _ = _noalloc(lib, mixed, A, spins[:, :16])
     assert rc == _lib.PEPS_EINVAL
+
+
+def test_noalloc_reuses_slots_for_more_samples_than_fit(lib):
+    """More samples than the scratch holds at once: 8x8, D=4, Dc=16 fits 39
+    per-sample workspaces, so 64 samples run on 39 slots, some slots taking
+    two samples in turn (the grid-stride loop), twice in a row."""
+    from paper_1806_03761_gb300 import PepsContext, _lib
+    L, D, Dc = 8, 4, 16
+    A = torch.from_numpy(make_peps(L, D, seed=2, kind="neel")).cuda()
+    shape = _lib.PepsShape(L, D, Dc, 1.0, 0.5, _lib.PEPS_FP64)
+    ctx = PepsContext(L, D, Dc, precision="fp64")
+    ctx.set_tensors(A)
+    for call in range(2):
+        spins = torch.from_numpy(random_sz0_configs(L, 64, seed=40 + call)).cuda()
+        rc, la, sg = _noalloc(lib, shape, A, spins)
+        assert rc == _lib.PEPS_OK
+        ref_la, ref_sg = ctx.amplitudes(spins)
+        torch.cuda.synchronize()
+        assert torch.equal(sg, ref_sg)
+        assert float((la - ref_la).abs().max()) <= TOL
+    ctx.close()
