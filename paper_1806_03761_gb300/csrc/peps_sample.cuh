@@ -72,6 +72,10 @@ __device__ __forceinline__ int sweep_one(const PepsPlan& P, const PepsStep* step
     __syncthreads();
     for (int j = 0; j + 1 < L; ++j) {
       int m = i * L + j;
+      // the left environment over column j with the current spins: the
+      // denominator's first column step when a move is proposed here (the
+      // numerator's when it is accepted), else computed on its own
+      R* out = w.l1 + (int64_t)(j + 1) * SC;
       if (sp[m] != sp[m + 1]) {
         Col1 kc0 = col_dims(P, Ud, Dd, j), kc1 = col_dims(P, Ud, Dd, j + 1);
         int n = env1_size(P, Ud, Dd, j + 2);
@@ -80,14 +84,18 @@ __device__ __forceinline__ int sweep_one(const PepsPlan& P, const PepsStep* step
         strip1_left_step<R>(P, kc0, Lj, U + j * SC, tens(P, As, m, sp[m + 1]), Dn + j * SC, w.y, w);
         strip1_left_step<R>(P, kc1, w.y, U + (j + 1) * SC, tens(P, As, m + 1, sp[m]), Dn + (j + 1) * SC, w.xj, w);
         double num = dot_blk<R>(w.xj, Rr, n, w);
-        strip1_left_step<R>(P, kc0, Lj, U + j * SC, tens(P, As, m, sp[m]), Dn + j * SC, w.y, w);
-        strip1_left_step<R>(P, kc1, w.y, U + (j + 1) * SC, tens(P, As, m + 1, sp[m + 1]), Dn + (j + 1) * SC, w.xj, w);
+        strip1_left_step<R>(P, kc0, Lj, U + j * SC, tens(P, As, m, sp[m]), Dn + j * SC, out, w);
+        strip1_left_step<R>(P, kc1, out, U + (j + 1) * SC, tens(P, As, m + 1, sp[m + 1]), Dn + (j + 1) * SC, w.xj, w);
         double den = dot_blk<R>(w.xj, Rr, n, w);
         double r = num / den;
         u32x4 ctr = {(uint32_t)(i * (L - 1) + j), sweep, chain, 1u};
         double u = uniform53(philox_word64(philox4x32_10(ctr, k0, k1)));
         if (!isfinite(r) && threadIdx.x == 0) atomicOr(w.flags, 1);
         if (u < r * r) {
+          // accepted: column j now carries the other spin, whose column
+          // step is the numerator's first one
+          const int n1 = env1_size(P, Ud, Dd, j + 1);
+          for (int o = threadIdx.x; o < n1; o += blockDim.x) out[o] = w.y[o];
           __syncthreads();
           if (threadIdx.x == 0) {
             uint8_t tmp = sp[m]; sp[m] = sp[m + 1]; sp[m + 1] = tmp;
@@ -95,11 +103,10 @@ __device__ __forceinline__ int sweep_one(const PepsPlan& P, const PepsStep* step
           }
           __syncthreads();
         }
+      } else {
+        Col1 k = col_dims(P, Ud, Dd, j);
+        strip1_left_step<R>(P, k, w.l1 + (int64_t)j * SC, U + j * SC, tens(P, As, m, sp[m]), Dn + j * SC, out, w);
       }
-      // advance the left environment over column j with the current spins
-      Col1 k = col_dims(P, Ud, Dd, j);
-      R* out = w.l1 + (int64_t)(j + 1) * SC;
-      strip1_left_step<R>(P, k, w.l1 + (int64_t)j * SC, U + j * SC, tens(P, As, m, sp[m]), Dn + j * SC, out, w);
       normalize_pow2<R>(out, env1_size(P, Ud, Dd, j + 1), w.red);
     }
     if (i + 1 < L) {
@@ -113,6 +120,10 @@ __device__ __forceinline__ int sweep_one(const PepsPlan& P, const PepsStep* step
         int m1 = i * L + j, m2 = m1 + L;
         Col1 k = col_dims(P, Ud, Dd2, j);
         const R* L2j = w.l2 + (int64_t)j * EC;
+        // the left environment over column j with the current spins: the
+        // denominator when a move is proposed here (the numerator when it is
+        // accepted), else computed on its own
+        R* out = w.l2 + (int64_t)(j + 1) * EC;
         if (sp[m1] != sp[m2]) {
           int n = env2_size(P, Ud, Dd2, j + 1);
           const R* Rr = w.r2 + (int64_t)(j + 1) * EC;
@@ -120,13 +131,14 @@ __device__ __forceinline__ int sweep_one(const PepsPlan& P, const PepsStep* step
                               tens(P, As, m2, sp[m1]), Dn2 + j * SC, w.y, w);
           double num = dot_blk<R>(w.y, Rr, n, w);
           strip2_left_step<R>(P, k, L2j, U + j * SC, tens(P, As, m1, sp[m1]),
-                              tens(P, As, m2, sp[m2]), Dn2 + j * SC, w.y, w);
-          double den = dot_blk<R>(w.y, Rr, n, w);
+                              tens(P, As, m2, sp[m2]), Dn2 + j * SC, out, w);
+          double den = dot_blk<R>(out, Rr, n, w);
           double r = num / den;
           u32x4 ctr = {(uint32_t)(L * (L - 1) + i * L + j), sweep, chain, 1u};
           double u = uniform53(philox_word64(philox4x32_10(ctr, k0, k1)));
           if (!isfinite(r) && threadIdx.x == 0) atomicOr(w.flags, 1);
           if (u < r * r) {
+            for (int o = threadIdx.x; o < n; o += blockDim.x) out[o] = w.y[o];
             __syncthreads();
             if (threadIdx.x == 0) {
               uint8_t tmp = sp[m1]; sp[m1] = sp[m2]; sp[m2] = tmp;
@@ -134,10 +146,10 @@ __device__ __forceinline__ int sweep_one(const PepsPlan& P, const PepsStep* step
             }
             __syncthreads();
           }
+        } else {
+          strip2_left_step<R>(P, k, L2j, U + j * SC, tens(P, As, m1, sp[m1]),
+                              tens(P, As, m2, sp[m2]), Dn2 + j * SC, out, w);
         }
-        R* out = w.l2 + (int64_t)(j + 1) * EC;
-        strip2_left_step<R>(P, k, L2j, U + j * SC, tens(P, As, m1, sp[m1]),
-                            tens(P, As, m2, sp[m2]), Dn2 + j * SC, out, w);
         normalize_pow2<R>(out, env2_size(P, Ud, Dd2, j + 1), w.red);
       }
       // ---- absorb the updated row i into the upper environment -----------
