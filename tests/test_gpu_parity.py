@@ -4,12 +4,10 @@ element by element, on seeded synthetic inputs.
 Tolerances: FP64 form 1e-10, mixed (float-float) form 1e-4 -- relative on
 E(S), on W(S) as |dlog|W|| with equal signs, on every flip ratio (with an
 absolute floor of tol * RMS of the sample's ratios) and on the Delta sums
-(relative to their largest entry).  Where the amplitude itself is
-ill-conditioned (heavy cancellation in W(S)), two backward-stable FP64
-evaluations cannot agree to 1e-10; there (``conditioned=True``) the FP64 bound
-of each quantity becomes max(1e-10, 100 * s), s being the oracle's own change
-when its input is perturbed by one unit roundoff (relative 2^-52, seeded).
-Integer outputs (signs, flip counts, sampled spins) must match exactly."""
+(relative to their largest entry).  Integer outputs (signs, flip counts,
+sampled spins) must match exactly.  The 16x16, D=6, Dc=24 workload, whose
+amplitudes are ill-conditioned, is compared with the oracle's stored results
+under a conditioning-aware bound in test_gpu_golden.py."""
 import numpy as np
 import pytest
 
@@ -35,28 +33,7 @@ def ctx_for(L, D, Dc, prec, slots=0, J2=0.5):
     return PepsContext(L, D, Dc, J1=1.0, J2=J2, precision=prec, slots=slots)
 
 
-def _errors(ref, other, spins, L, D, delta, tol):
-    """Per-quantity errors of `other` against `ref` (both oracle-style dicts)."""
-    err = dict(log_abs=np.max(np.abs(other["log_abs"] - ref["log_abs"])),
-               e_loc=np.max(np.abs(other["e_loc"] - ref["e_loc"]) / np.maximum(1.0, np.abs(ref["e_loc"]))))
-    for b in range(len(spins)):
-        rr = ref["ratios"][b]
-        m = rr != 0
-        if m.any():
-            floor = tol * np.sqrt(np.mean(rr[m] ** 2))
-            err["ratios"] = max(err.get("ratios", 0.0),
-                                np.max(np.abs(other["ratios"][b][m] - rr[m]) / np.maximum(np.abs(rr[m]), floor / tol)))
-    return err
-
-
-def sensitivity(A, spins, L, Dc, delta):
-    """The oracle's change under a one-unit-roundoff relative perturbation of A."""
-    rng = np.random.default_rng(1234)
-    Ap = A * (1.0 + 2.0 ** -52 * rng.standard_normal(A.shape))
-    return Ap
-
-
-def check_eval(A, spins, L, D, Dc, prec, slots=0, delta=True, conditioned=False):
+def check_eval(A, spins, L, D, Dc, prec, slots=0, delta=True):
     tol = TOL[prec]
     ctx = ctx_for(L, D, Dc, prec, slots)
     ctx.set_tensors(torch.from_numpy(A).cuda())
@@ -100,15 +77,6 @@ def check_eval(A, spins, L, D, Dc, prec, slots=0, delta=True, conditioned=False)
         dr = np.stack([ref["delta"][b, np.arange(N), spins[b]].reshape(N, -1) for b in range(len(spins))])
         err["delta"] = np.max(np.abs(dg - dr)) / np.abs(dr).max()
     bound = {k: tol for k in err}
-    if conditioned and prec == "fp64":
-        Ap = sensitivity(A, spins, L, Dc, delta)
-        refp = oracle.evaluate_batch(Ap, spins, L, Dc, want_delta=delta)
-        sens = _errors(ref, refp, spins, L, D, delta, tol)
-        if delta:
-            sens["sum_delta"] = sens["sum_delta_e"] = sens["delta"] = max(sens.values())
-            sens["sum_e"] = sens["e_loc"]
-        bound = {k: max(tol, 100.0 * sens.get(k, 0.0)) for k in err}
-        print("  sensitivity to one unit roundoff:", {k: "%.2e" % v for k, v in sens.items()})
     print(prec, L, D, Dc, {k: "%.2e" % v for k, v in err.items()})
     for k, v in err.items():
         assert v <= bound[k], (k, v, bound[k])
@@ -137,20 +105,17 @@ def test_parity_8x8_D4_Dc16_neel(prec):
     check_eval(A, spins, 8, 4, 16, prec)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_parity_16x16_D6_Dc24(prec):
-    A = make_peps(16, 6, seed=4)
-    spins = random_sz0_configs(16, 2, seed=5)
-    check_eval(A, spins, 16, 6, 24, prec, conditioned=True)
-
-
 def test_full_wave_16x16_in_the_bench_launch():
     # the bench's launch configuration: one wave of 304 chains on the default
     # slots, both forms; every output compared across forms (a property at
-    # any size) and three sampled outputs against the oracle
+    # any size) and the first 64 against the oracle's stored results (the
+    # golden configurations are the workload's first 64)
+    from tests.test_gpu_golden import GOLD, check_against_gold
     L, D, Dc, B = 16, 6, 24, 304
     A = make_peps(L, D, seed=4)
     spins = random_sz0_configs(L, B, seed=5)
+    g = dict(np.load(GOLD))
+    assert np.array_equal(g["spins"], spins[:64])
     sp = torch.from_numpy(spins).cuda()
     res = {}
     for prec in ("fp64", "mixed"):
@@ -168,20 +133,11 @@ def test_full_wave_16x16_in_the_bench_launch():
     print("mixed vs fp64 over the wave: max %.2e median %.2e" % (de.max(), np.median(de)))
     assert de.max() <= TOL["mixed"]
     assert np.max(np.abs(res["mixed"]["log_abs"] - res["fp64"]["log_abs"])) <= TOL["mixed"]
-    rng = np.random.default_rng(1234)
-    Ap = A * (1.0 + 2.0 ** -52 * rng.standard_normal(A.shape))
-    for b in (0, 151, 303):
-        o = oracle.evaluate(A, spins[b], L, Dc)
-        op = oracle.evaluate(Ap, spins[b], L, Dc)
-        s_e = abs(op["e_loc"] - o["e_loc"]) / max(1.0, abs(o["e_loc"]))
-        s_l = abs(op["log_abs"] - o["log_abs"])
-        for prec in ("fp64", "mixed"):
-            assert res[prec]["sign"][b] == o["sign"]
-            ge = abs(res[prec]["e_loc"][b] - o["e_loc"]) / max(1.0, abs(o["e_loc"]))
-            gl = abs(res[prec]["log_abs"][b] - o["log_abs"])
-            be, bl = max(TOL[prec], 100.0 * s_e), max(TOL[prec], 100.0 * s_l)
-            print(prec, b, "e %.2e (bound %.2e)  log|W| %.2e (bound %.2e)" % (ge, be, gl, bl))
-            assert ge <= be and gl <= bl
+    for prec in ("fp64", "mixed"):
+        errs = check_against_gold(g, res[prec], prec, first=64)
+        print(prec, "first 64 vs oracle:", {k: "%.2e (%.2f of bound)" % v for k, v in errs.items()})
+        for k, (e, ratio) in errs.items():
+            assert ratio <= 1.0, (prec, k, e, ratio)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
@@ -265,6 +221,26 @@ def test_sampler_bit_exact(prec, L, D, Dc):
     ref2, fin2, _ = oracle.sample_chains(A, L, Dc, 12345678901, 3, 0, 1, 2, init=fin, first_sweep=10)
     assert np.array_equal(out2.cpu().numpy(), ref2)
     assert np.array_equal(state.cpu().numpy(), fin2)
+    ctx.close()
+
+
+@pytest.mark.parametrize("kind", ["neel", "gauss"])
+def test_sampler_bit_exact_8x8_fp64(kind):
+    """FP64 form, 8x8, D=4, Dc=16 (multi-panel QR and blocked
+    bidiagonalisation in every compression): two sweeps of three chains give
+    the oracle's configurations and acceptance counts bit for bit."""
+    L, D, Dc = 8, 4, 16
+    A = make_peps(L, D, seed=2, kind=kind)
+    ctx = ctx_for(L, D, Dc, "fp64", slots=3)
+    ctx.set_tensors(torch.from_numpy(A).cuda())
+    seed = 0x5EED0002
+    out, acc = ctx.sample(seed=seed, n_chains=3, n_burn=1, n_thin=1, samples_per_chain=1,
+                          accepted=True)
+    ref, fin, racc = oracle.sample_chains(A, L, Dc, seed, 3, 1, 1, 1)
+    assert np.array_equal(out.cpu().numpy(), ref)
+    assert np.array_equal(acc.cpu().numpy(), racc)
+    assert racc.sum() > 0  # some exchanges were accepted
+    assert ctx.sync_status()[0] == 0
     ctx.close()
 
 
