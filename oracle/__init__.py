@@ -22,3 +22,6 @@ from .peps import (  # noqa: F401
 )
 from .philox import philox4x32_10, uniform53, uniform_open53  # noqa: F401
 from .sampler import init_config, metropolis_sweep, sample_chains  # noqa: F401
+from .correlations import (  # noqa: F401
+    exchange_ratios, local_correlations, bulk_sites, structure_factor, centre_site,
+)

@@ -168,3 +168,24 @@ def dense_H(L, J1, J2):
             H += J * op(o, a) @ op(o, b)
     assert np.allclose(H.imag, 0)
     return H.real
+
+
+def dense_SS(L, a, b):
+    """S_a . S_b as a dense matrix (Kronecker products of the spin-1/2
+    matrices; bit m <-> site m, |0> = up).  a == b gives 3/4 times 1."""
+    N = L * L
+    sx = np.array([[0, 0.5], [0.5, 0]])
+    sy = np.array([[0, -0.5j], [0.5j, 0]])
+    sz = np.array([[0.5, 0], [0, -0.5]])
+
+    def op(o, m):
+        mats = [np.eye(2)] * N
+        mats[N - 1 - m] = o
+        r = np.array([[1.0]])
+        for M in mats:
+            r = np.kron(r, M)
+        return r
+
+    S = sum(op(o, a) @ op(o, b) for o in (sx, sy, sz))
+    assert np.allclose(S.imag, 0)
+    return S.real
