@@ -226,6 +226,34 @@ int peps_vmc_step(peps_ctx* ctx, uint64_t seed, int64_t n_chains,
                   double* sum_delta, double* sum_delta_e, double* sum_e,
                   int32_t accumulate, int64_t* accepted, void* stream);
 
+/* Spin-spin correlations (Sec. "Experiment Setup" and the results after it:
+ * the map <S_0 . S_m> and the structure factor m_s^2(k)).  For every sample b
+ * and source site src[q], the local values of S_src . S_m at every site m,
+ *     ss[b][q][m] = sigma_src sigma_m / 4 + [s_src != s_m] W(S')/W(S) / 2,
+ * ss[b][q][src] = 3/4, S' = S with s_src and s_m exchanged; their mean over
+ * configurations drawn from W^2 is <S_src . S_m>.  The ratio is taken on the
+ * one-row strip of row i(m), each configuration with its own environments
+ * (W_i(S') / W_i(S); for a pair in one row the horizontal-bond window).
+ *   spins: uint8[B][N] (device); src: int32[n_src] (HOST), 1 <= n_src <= N,
+ *   0 <= src[q] < N; ss: float64[B][n_src][N] (device, written);
+ *   ss_mean: float64[n_src][N] (device, nullable): the mean over the batch,
+ *   summed in sample order (bit-reproducible).
+ * FP64 and mixed forms (PEPS_EINVAL for PEPS_FP32).  Items (sample, source)
+ * run one per thread block; each costs about one evaluation.  Zero or
+ * non-finite amplitudes set PEPS_FLAG_NONFINITE (ratio 0).  The source list is
+ * copied into the context: calls on one context are ordered on one stream. */
+int peps_correlations(peps_ctx* ctx, const uint8_t* spins, int64_t B, int32_t n_src,
+                      const int32_t* src, double* ss, double* ss_mean, void* stream);
+
+/* m_s^2(k) = (1/n^2) sum_{a, m in the bulk} C[a][m] cos(k . (r_a - r_m)) over
+ * the n = (L-4)^2 central sites (all sites for L <= 4), C[a][m] =
+ * ss_mean[q(a)][m] from peps_correlations with sources src (HOST int32[n_src];
+ * every bulk site must be among them, else PEPS_EINVAL); k = (kx, ky) along
+ * (rows, columns); M^2 = m_s^2(pi, pi).  m2: float64[1] (device, written). */
+int peps_structure_factor(peps_ctx* ctx, const double* ss_mean, int32_t n_src,
+                          const int32_t* src, double kx, double ky, double* m2,
+                          void* stream);
+
 /* Wait for `stream` and return the device-side error state: PEPS_OK, or
  * PEPS_ENUMERIC with *flags (host, nullable) set to the PEPS_FLAG_* bits
  * seen since the last call (the bits are cleared). */

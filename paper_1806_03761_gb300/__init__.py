@@ -200,6 +200,33 @@ class PepsContext:
         res.update(sum_delta=sums[0], sum_delta_e=sums[1], sum_e=sums[2], accepted=acc)
         return res
 
+    def correlations(self, spins, sources, mean=True):
+        """Local values of S_src . S_m (peps_correlations): returns
+        dict(ss=float64[B][n_src][N], mean=float64[n_src][N] or None)."""
+        import numpy as np
+        t = self.torch
+        s = self._spins(spins)
+        B = s.shape[0]
+        src = np.ascontiguousarray(np.asarray(sources, dtype=np.int32).reshape(-1))
+        ss = self._empty(B, src.size, self.N)
+        mn = self._empty(src.size, self.N) if mean else None
+        self._check(self.lib.peps_correlations(self.h, _ptr(s), B, int(src.size),
+                                               src.ctypes.data_as(ctypes.c_void_p), _ptr(ss),
+                                               _ptr(mn), self._stream()))
+        return dict(ss=ss, mean=mn)
+
+    def structure_factor(self, mean, sources, k=(3.141592653589793, 3.141592653589793)):
+        """m_s^2(k) over the bulk from the batch means (peps_structure_factor);
+        a one-element float64 device tensor."""
+        import numpy as np
+        src = np.ascontiguousarray(np.asarray(sources, dtype=np.int32).reshape(-1))
+        out = self._empty(1)
+        self._check(self.lib.peps_structure_factor(self.h, _ptr(mean), int(src.size),
+                                                   src.ctypes.data_as(ctypes.c_void_p),
+                                                   float(k[0]), float(k[1]), _ptr(out),
+                                                   self._stream()))
+        return out
+
     def sync_status(self):
         f = ctypes.c_int32(0)
         rc = self.lib.peps_sync_status(self.h, self._stream(), ctypes.byref(f))

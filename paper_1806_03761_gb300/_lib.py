@@ -27,7 +27,8 @@ EXPORTS = ("peps_create", "peps_destroy", "peps_last_error", "peps_workspace_byt
            "peps_set_tensors", "peps_amplitudes", "peps_local_energy", "peps_logderiv",
            "peps_evaluate", "peps_grad_step", "peps_sample_batch", "peps_sync_status",
            "peps_flops_per_sample", "peps_amplitudes_noalloc", "peps_vmc_step",
-           "peps_server_create", "peps_server_submit", "peps_server_wait", "peps_server_destroy")
+           "peps_server_create", "peps_server_submit", "peps_server_wait", "peps_server_destroy",
+           "peps_correlations", "peps_structure_factor")
 
 
 class PepsShape(ctypes.Structure):
@@ -79,6 +80,8 @@ _SIGS = {
     "peps_server_submit": (I32, [P, ctypes.POINTER(PepsJob), ctypes.POINTER(I64)]),
     "peps_server_wait": (I32, [P, I64, F64, ctypes.POINTER(PepsJobStats)]),
     "peps_server_destroy": (I32, [P]),
+    "peps_correlations": (I32, [P, P, I64, I32, P, P, P, P]),
+    "peps_structure_factor": (I32, [P, P, I32, P, F64, F64, P, P]),
 }
 
 

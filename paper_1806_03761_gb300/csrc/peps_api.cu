@@ -23,6 +23,7 @@ struct peps_ctx {
   double* wsd = nullptr;   // slot double workspaces
   double* psum = nullptr;  // slot partial sums
   int* flags = nullptr;
+  int32_t* idx = nullptr;  // 3N int32: correlation sources, bulk positions, bulk sites
   int nslots = 0;
   int tensors_set = 0;
   int device = 0;
@@ -62,6 +63,8 @@ cudaError_t launch_sample_form(const SampleArgs<float>& a, int g, cudaStream_t s
 cudaError_t launch_vmc_form(const EvalArgs<double>& a, const SampleArgs<double>& b, int g, cudaStream_t s) { return peps_launch_vmc_f64(a, b, g, s); }
 cudaError_t launch_vmc_form(const EvalArgs<ff>& a, const SampleArgs<ff>& b, int g, cudaStream_t s) { return peps_launch_vmc_ff(a, b, g, s); }
 cudaError_t launch_vmc_form(const EvalArgs<float>& a, const SampleArgs<float>& b, int g, cudaStream_t s) { return peps_launch_vmc_f32(a, b, g, s); }
+cudaError_t launch_corr_form(const CorrArgs<double>& a, int g, cudaStream_t s) { return peps_launch_corr_f64(a, g, s); }
+cudaError_t launch_corr_form(const CorrArgs<ff>& a, int g, cudaStream_t s) { return peps_launch_corr_ff(a, g, s); }
 
 // Bond dimensions of every absorption step and the slot layout (peps_plan.h).
 void make_plan(const peps_shape& s, int nslots, PepsPlan* P, std::vector<PepsStep>* steps) {
@@ -218,6 +221,37 @@ int launch_vmc(peps_ctx* c, uint64_t seed, int64_t n, int64_t chain_offset, uint
   return PEPS_OK;
 }
 
+template <class R>
+int launch_corr(peps_ctx* c, const uint8_t* spins, int64_t B, int32_t n_src, double* ss,
+                cudaStream_t st) {
+  CorrArgs<R> a;
+  std::memset(&a, 0, sizeof(a));
+  a.P = c->plan;
+  a.steps = c->steps;
+  a.As = static_cast<const R*>(c->As);
+  a.spins = spins;
+  a.B = B;
+  a.n_src = n_src;
+  a.src = c->idx;
+  a.ss = ss;
+  a.ws = static_cast<R*>(c->ws);
+  a.wsd = c->wsd;
+  a.flags = c->flags;
+  int grid = (int)std::min<int64_t>(c->nslots, B * n_src);
+  cudaError_t e = launch_corr_form(a, grid, st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "peps_corr_kernel launch");
+  return PEPS_OK;
+}
+
+// The central (L-4) x (L-4) sites, every site when L <= 4.
+std::vector<int32_t> bulk_list(int L) {
+  const int lo = L > 4 ? 2 : 0, hi = L > 4 ? L - 2 : L;
+  std::vector<int32_t> b;
+  for (int i = lo; i < hi; ++i)
+    for (int j = lo; j < hi; ++j) b.push_back(i * L + j);
+  return b;
+}
+
 }  // namespace
 
 extern "C" {
@@ -262,7 +296,8 @@ int peps_create(const peps_shape* shape, int32_t slots, peps_ctx** out) {
             cudaMalloc(&c->ws, (size_t)slots * P.slot_elems * es) == cudaSuccess &&
             cudaMalloc(&c->wsd, (size_t)slots * P.slot_doubles * 8) == cudaSuccess &&
             cudaMalloc(&c->psum, (size_t)slots * psum_len(P) * 8) == cudaSuccess &&
-            cudaMalloc(&c->flags, sizeof(int)) == cudaSuccess;
+            cudaMalloc(&c->flags, sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&c->idx, 3 * (size_t)P.N * sizeof(int32_t)) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     peps_destroy(c);
@@ -287,6 +322,7 @@ int peps_destroy(peps_ctx* c) {
   cudaFree(c->wsd);
   cudaFree(c->psum);
   cudaFree(c->flags);
+  cudaFree(c->idx);
   delete c;
   return PEPS_OK;
 }
@@ -407,6 +443,56 @@ int peps_vmc_step(peps_ctx* c, uint64_t seed, int64_t n_chains, int64_t chain_of
                              sum_delta, sum_delta_e, sum_e, accumulate, accepted, st);
   return launch_vmc<ff>(c, seed, n_chains, chain_offset, sweep, chain_state, e_loc, log_abs, sign,
                         sum_delta, sum_delta_e, sum_e, accumulate, accepted, st);
+}
+
+int peps_correlations(peps_ctx* c, const uint8_t* spins, int64_t B, int32_t n_src,
+                      const int32_t* src, double* ss, double* ss_mean, void* stream) {
+  if (!c) return PEPS_EINVAL;
+  const int N = c->plan.N;
+  if (B < 0) return fail(c, PEPS_EINVAL, "B must be >= 0");
+  if (n_src < 1 || n_src > N || !src) return fail(c, PEPS_EINVAL, "need 1 <= n_src <= N sources");
+  for (int q = 0; q < n_src; ++q)
+    if (src[q] < 0 || src[q] >= N) return fail(c, PEPS_EINVAL, "source sites must lie in [0, N)");
+  if (c->shape.precision == PEPS_FP32)
+    return fail(c, PEPS_EINVAL, "correlations are computed in the FP64 and mixed forms");
+  if (!c->tensors_set) return fail(c, PEPS_EINVAL, "peps_set_tensors has not been called");
+  if (B == 0) return PEPS_OK;
+  if (!spins || !ss) return fail(c, PEPS_EINVAL, "spins and ss are required");
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, PEPS_ECUDA, "cudaSetDevice failed");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(c->idx, src, (size_t)n_src * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "copying the source sites");
+  int rc = c->shape.precision == PEPS_FP64 ? launch_corr<double>(c, spins, B, n_src, ss, st)
+                                           : launch_corr<ff>(c, spins, B, n_src, ss, st);
+  if (rc != PEPS_OK || !ss_mean) return rc;
+  e = peps_launch_corr_mean(ss, B, (int64_t)n_src * N, ss_mean, st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "peps_corr_mean launch");
+  return PEPS_OK;
+}
+
+int peps_structure_factor(peps_ctx* c, const double* ss_mean, int32_t n_src, const int32_t* src,
+                          double kx, double ky, double* m2, void* stream) {
+  if (!c) return PEPS_EINVAL;
+  const int L = c->plan.L, N = c->plan.N;
+  if (!ss_mean || !m2 || !src || n_src < 1 || n_src > N)
+    return fail(c, PEPS_EINVAL, "ss_mean, src (1 <= n_src <= N) and m2 are required");
+  if (!std::isfinite(kx) || !std::isfinite(ky)) return fail(c, PEPS_EINVAL, "k must be finite");
+  std::vector<int32_t> bulk = bulk_list(L), pos(bulk.size(), -1);
+  for (size_t t = 0; t < bulk.size(); ++t)
+    for (int q = 0; q < n_src; ++q)
+      if (src[q] == bulk[t]) { pos[t] = q; break; }
+  for (int32_t p : pos)
+    if (p < 0) return fail(c, PEPS_EINVAL, "every bulk site must be among the sources");
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, PEPS_ECUDA, "cudaSetDevice failed");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t nb = bulk.size() * sizeof(int32_t);
+  cudaError_t e = cudaMemcpyAsync(c->idx + N, pos.data(), nb, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->idx + 2 * N, bulk.data(), nb, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "copying the bulk sites");
+  e = peps_launch_structure_factor(ss_mean, L, N, c->idx + N, (int)bulk.size(), c->idx + 2 * N,
+                                   kx, ky, m2, st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "peps_structure_factor launch");
+  return PEPS_OK;
 }
 
 int peps_sync_status(peps_ctx* c, void* stream, int32_t* flags) {

@@ -41,3 +41,19 @@ struct SampleArgs {
   double* wsd;
   int* flags;
 };
+
+// Spin correlations: items (sample b, source q), b < B, q < n_src.
+template <class R>
+struct CorrArgs {
+  PepsPlan P;
+  const PepsStep* steps;
+  const R* As;
+  const uint8_t* spins;   // [B][N]
+  int64_t B;
+  int n_src;
+  const int32_t* src;     // [n_src] source sites, validated on the host
+  double* ss;             // [B][n_src][N] local values of S_src . S_m
+  R* ws;
+  double* wsd;
+  int* flags;
+};

@@ -18,7 +18,9 @@
 #define PEPS_HD __device__ __forceinline__
 #endif
 
-struct ff {
+// 8-byte aligned so that a value moves in one 64-bit load or store (every ff
+// array in the workspaces and in shared memory starts on an 8-byte boundary)
+struct __align__(8) ff {
   float hi, lo;
 };
 

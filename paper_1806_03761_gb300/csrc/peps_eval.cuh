@@ -33,6 +33,8 @@ __device__ Work<R> make_work(const PepsPlan& P, R* ws, double* wsd, int slot) {
   w.delta = bd + P.doff_delta;
   w.alpha = base + P.off_alpha;
   w.inv = base + P.off_inv;
+  w.dnf = base + P.off_dnf;
+  w.upf = base + P.off_upf;
   return w;
 }
 
@@ -226,8 +228,11 @@ struct BlockShared {
   __align__(16) unsigned char qrv_raw[PEPS_QR_NB * PEPS_QR_ROWS * sizeof(R)];
   double rot[512];
   uint8_t sp[PEPS_MAXL * PEPS_MAXL];
+  uint8_t sp2[PEPS_MAXL * PEPS_MAXL];  // a second configuration (correlations)
   double dnlog[PEPS_MAXL + 1];
+  double dnlogf[PEPS_MAXL + 1];
   double uplog[3];
+  double uplogf[3];
   int count;
 };
 

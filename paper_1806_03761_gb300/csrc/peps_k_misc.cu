@@ -50,3 +50,48 @@ cudaError_t peps_launch_grad(int precision, const double* sd, const double* sde,
                                                static_cast<ff*>(As), n);
   return cudaGetLastError();
 }
+
+// mean[k] = (1/B) sum_b ss[b][k], b in order (bit-reproducible)
+__global__ void peps_corr_mean(const double* ss, int64_t B, int64_t len, double* mean) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < len; k += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int64_t b = 0; b < B; ++b) s += ss[b * len + k];
+    mean[k] = s / (double)B;
+  }
+}
+
+cudaError_t peps_launch_corr_mean(const double* ss, int64_t B, int64_t len, double* mean,
+                                  cudaStream_t st) {
+  int grid = (int)((len + 255) / 256 < 4096 ? (len + 255) / 256 : 4096);
+  peps_corr_mean<<<grid, 256, 0, st>>>(ss, B, len, mean);
+  return cudaGetLastError();
+}
+
+// m_s^2(k) = (1/n^2) sum_{a, m in bulk} C[pos[a]][m] cos(k . (r_a - r_m)): one
+// block, each thread a fixed set of (a, m) pairs, then a fixed-order tree.
+__global__ void peps_structure_factor_kernel(const double* mean, int L, int N, const int32_t* pos,
+                                             int nbulk, const int32_t* bulk, double kx, double ky,
+                                             double* out) {
+  __shared__ double red[256];
+  double s = 0.0;
+  const int64_t pairs = (int64_t)nbulk * nbulk;
+  for (int64_t t = threadIdx.x; t < pairs; t += blockDim.x) {
+    const int a = bulk[t / nbulk], m = bulk[t % nbulk];
+    const int ia = a / L, ja = a % L, im = m / L, jm = m % L;
+    s += mean[(int64_t)pos[t / nbulk] * N + m] * cos(kx * (ia - im) + ky * (ja - jm));
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0] / ((double)nbulk * (double)nbulk);
+}
+
+cudaError_t peps_launch_structure_factor(const double* mean, int L, int N, const int32_t* pos,
+                                         int nbulk, const int32_t* bulk, double kx, double ky,
+                                         double* out, cudaStream_t st) {
+  peps_structure_factor_kernel<<<1, 256, 0, st>>>(mean, L, N, pos, nbulk, bulk, kx, ky, out);
+  return cudaGetLastError();
+}

@@ -1,14 +1,8 @@
-// Metropolis sampling and fused VMC-step kernels, FP32 form.
+// Metropolis sampling kernel, f32 form.
 #include "peps_sample.cuh"
 #include "peps_launch.h"
 
 cudaError_t peps_launch_sample_f32(const SampleArgs<float>& a, int grid, cudaStream_t st) {
   peps_sample_kernel<float><<<grid, PEPS_NT, 0, st>>>(a);
-  return cudaGetLastError();
-}
-
-cudaError_t peps_launch_vmc_f32(const EvalArgs<float>& a, const SampleArgs<float>& s, int grid,
-                              cudaStream_t st) {
-  peps_vmc_kernel<float><<<grid, PEPS_NT, 0, st>>>(a, s);
   return cudaGetLastError();
 }

@@ -1,14 +1,8 @@
-// Metropolis sampling and fused VMC-step kernels, double form.
+// Metropolis sampling kernel, f64 form.
 #include "peps_sample.cuh"
 #include "peps_launch.h"
 
 cudaError_t peps_launch_sample_f64(const SampleArgs<double>& a, int grid, cudaStream_t st) {
   peps_sample_kernel<double><<<grid, PEPS_NT, 0, st>>>(a);
-  return cudaGetLastError();
-}
-
-cudaError_t peps_launch_vmc_f64(const EvalArgs<double>& a, const SampleArgs<double>& s, int grid,
-                              cudaStream_t st) {
-  peps_vmc_kernel<double><<<grid, PEPS_NT, 0, st>>>(a, s);
   return cudaGetLastError();
 }

@@ -1,14 +1,8 @@
-// Metropolis sampling and fused VMC-step kernels, ff form.
+// Metropolis sampling kernel, ff form.
 #include "peps_sample.cuh"
 #include "peps_launch.h"
 
 cudaError_t peps_launch_sample_ff(const SampleArgs<ff>& a, int grid, cudaStream_t st) {
   peps_sample_kernel<ff><<<grid, PEPS_NT, 0, st>>>(a);
-  return cudaGetLastError();
-}
-
-cudaError_t peps_launch_vmc_ff(const EvalArgs<ff>& a, const SampleArgs<ff>& s, int grid,
-                              cudaStream_t st) {
-  peps_vmc_kernel<ff><<<grid, PEPS_NT, 0, st>>>(a, s);
   return cudaGetLastError();
 }

@@ -7,6 +7,7 @@
 
 template <class R> struct EvalArgs;
 template <class R> struct SampleArgs;
+template <class R> struct CorrArgs;
 
 cudaError_t peps_launch_eval_f64(const EvalArgs<double>& a, int grid, cudaStream_t st);
 cudaError_t peps_launch_eval_ff(const EvalArgs<ff>& a, int grid, cudaStream_t st);
@@ -24,3 +25,10 @@ cudaError_t peps_launch_convert(int precision, const double* A, void* As, int64_
 cudaError_t peps_launch_grad(int precision, const double* sd, const double* sde, const double* se,
                              double M, double dt, uint32_t k0, uint32_t k1, uint32_t step,
                              double* A, void* As, int64_t n, cudaStream_t st);
+cudaError_t peps_launch_corr_f64(const CorrArgs<double>& a, int grid, cudaStream_t st);
+cudaError_t peps_launch_corr_ff(const CorrArgs<ff>& a, int grid, cudaStream_t st);
+cudaError_t peps_launch_corr_mean(const double* ss, int64_t B, int64_t len, double* mean,
+                                  cudaStream_t st);
+cudaError_t peps_launch_structure_factor(const double* mean, int L, int N, const int32_t* pos,
+                                         int nbulk, const int32_t* bulk, double kx, double ky,
+                                         double* out, cudaStream_t st);

@@ -34,6 +34,8 @@ struct Work {
   double* delta;  // staged Delta of one sample: N D^4
   R* alpha;       // singular-value scratch (d, e, tau of the bidiagonal)
   R* inv;         // inverse-iteration scratch
+  R* dnf;         // lower / upper environments of a configuration with one
+  R* upf;         // spin flipped (spin correlations)
   // shared memory
   double* red;
   R* redR;

@@ -46,7 +46,8 @@ struct PepsPlan {
   int64_t env2_cap;   // Dc*D*D*Dc: two-row strip environment
   // per-slot workspace offsets in scalars of the form's type
   int64_t off_dn, off_up, off_rst, off_b0, off_b1, off_b2, off_y, off_xj,
-      off_vt, off_c0, off_c1, off_l1, off_r1, off_l2, off_r2, off_alpha, off_inv, off_tmp;
+      off_vt, off_c0, off_c1, off_l1, off_r1, off_l2, off_r2, off_alpha, off_inv, off_tmp,
+      off_dnf, off_upf;
   int64_t slot_elems;  // scalars per slot
   // per-slot workspace offsets in doubles
   int64_t doff_scale, doff_delta, doff_alpha;
@@ -125,6 +126,9 @@ static inline void peps_plan_layout(PepsPlan* P, bool amplitude_only) {
   P->off_alpha = take(3 * (int64_t)Dc * D + 16);
   P->off_inv = take(13 * (int64_t)Dc * Dc * D);
   P->off_tmp = take(32);
+  // environments of a configuration with one spin flipped (correlations)
+  P->off_dnf = amplitude_only ? 0 : take((int64_t)(L + 1) * P->env_cap);
+  P->off_upf = amplitude_only ? 0 : take(3 * P->env_cap);
   P->slot_elems = o;
   int64_t d = 0;
   auto taked = [&](int64_t n) { int64_t r = d; d += peps_up32(n); return r; };

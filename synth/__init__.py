@@ -90,6 +90,10 @@ CONFIGS = {
                           config_seed=5, batch=8192),
     "24x24_D8_Dc32": dict(L=24, D=8, Dc=32, recipe="gauss", seed=6,
                           config_seed=7, batch=1024),
+    # a smaller lattice with the 16x16 workload's bond dimensions (the same
+    # QR and SVD shapes per site): profiling captures
+    "12x12_D6_Dc24": dict(L=12, D=6, Dc=24, recipe="gauss", seed=8,
+                          config_seed=9, batch=304),
 }
 
 
