@@ -61,8 +61,9 @@ def parse():
     p.add_argument("--slots", type=int, default=0)
     p.add_argument("--dt", type=float, default=1e-3)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--mode", default="vmc", choices=["vmc", "serving"],
-                   help="serving: a Poisson stream of evaluation jobs through peps_server_*")
+    p.add_argument("--mode", default="vmc", choices=["vmc", "serving", "contraction"],
+                   help="serving: a Poisson stream of evaluation jobs through peps_server_*; "
+                        "contraction: tensor-core vs CUDA-core column-step contractions")
     p.add_argument("--arrival-s", type=float, default=30.0,
                    help="serving: length of the arrival window per precision form")
     p.add_argument("--rate", type=float, default=1.0, help="serving: job arrivals per second")
@@ -271,8 +272,72 @@ def run_serving(args):
     print(json.dumps(line), flush=True)
 
 
+# Column-step contractions of the 16x16, D=6, Dc=24 workload as (M, N, K):
+# C[M][N] = A[M][K] B[K][N] (strip step G2/G3 and the absorption's X,
+# the strip step G1 and the absorption's S1, the strip closing step).
+CONTRACTIONS = [(3456, 36, 36), (864, 144, 24), (864, 24, 144)]
+
+
+def run_contraction(args):
+    """--mode contraction: each column-step shape, batch = one contraction per
+    slot of the persistent kernel, on the tensor cores (peps_tc_gemm: split +
+    MMA) and on the CUDA cores (peps_cc_gemm: contract() in float-float and in
+    FP64, operands converted beforehand); device time per batch (CUDA events,
+    mean of --steps after --warmup) and the worst error against the FP64
+    product relative to sum |a||b| on 4 batch elements."""
+    import torch
+
+    import paper_1806_03761_gb300 as P
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    batch = args.batch or 2 * sms
+    rng = np.random.default_rng(2024)
+    stream = torch.cuda.current_stream()
+    rows = []
+    for (M, N, K) in CONTRACTIONS:
+        A = torch.from_numpy(rng.standard_normal((batch, M, K))).cuda()
+        Bm = torch.from_numpy(rng.standard_normal((batch, K, N))).cuda()
+        c = P.Contraction(M, N, K, batch, slices=7)
+        An, Bn = A[:4].cpu().numpy(), Bm[:4].cpu().numpy()
+        exact = np.einsum("bmk,bkn->bmn", An, Bn)
+        scale = np.einsum("bmk,bkn->bmn", np.abs(An), np.abs(Bn))
+        res = {"M": M, "N": N, "K": K, "batch": batch}
+        for name, fn in (("tensor_cores", lambda: c.tensor_cores(A, Bm, C)),
+                         ("cuda_cores_ff", lambda: c.cuda_cores(A, Bm, "mixed", C, convert=False)),
+                         ("cuda_cores_fp64", lambda: c.cuda_cores(A, Bm, "fp64", C, convert=False))):
+            C = torch.empty(batch, M, N, dtype=torch.float64, device="cuda")
+            if name != "tensor_cores":  # operands converted once, outside the timing
+                c.cuda_cores(A, Bm, "mixed" if name.endswith("ff") else "fp64", C, convert=True)
+            for _ in range(args.warmup):
+                fn()
+            torch.cuda.synchronize()
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            for _ in range(args.steps):
+                fn()
+            t1.record(stream)
+            torch.cuda.synchronize()
+            ms = t0.elapsed_time(t1) / max(args.steps, 1)
+            if name != "tensor_cores":
+                c.cuda_cores(A, Bm, "mixed" if name.endswith("ff") else "fp64", C, convert=True)
+            else:
+                fn()
+            torch.cuda.synchronize()
+            err = float(np.max(np.abs(C[:4].cpu().numpy() - exact) / scale))
+            res[name] = {"ms": ms, "tflops": 2.0 * M * N * K * batch / (ms / 1e3) / 1e12, "err": err}
+        res["status"] = int(c.status.item())
+        rows.append(res)
+    line = {"metric": "column-step contraction time, tensor cores (tcgen05, 7 BF16 slices) vs CUDA cores",
+            "unit": "ms per batch", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "data": "synthetic (N(0,1) operands)", "config": {"workload": "16x16_D6_Dc24 column steps",
+                                                              "batch": batch}, "shapes": rows}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.mode == "contraction":
+        run_contraction(args)
+        return
     cfg = dict(CONFIGS[args.workload])
     if args.impl == "reference":
         run_reference(args, cfg)

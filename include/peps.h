@@ -254,6 +254,39 @@ int peps_structure_factor(peps_ctx* ctx, const double* ss_mean, int32_t n_src,
                           const int32_t* src, double kx, double ky, double* m2,
                           void* stream);
 
+/* Batched contraction C_b = A_b B_b (A_b: float64[M][K] row-major, B_b:
+ * float64[K][N] row-major, C_b: float64[M][N]; batch elements contiguous, B
+ * shared by the batch when b_shared = 1) on the tcgen05 tensor cores at
+ * FP64-class accuracy: every row of A and column of B is split error-free
+ * into `slices` BF16 integer slices of 7 bits at a common exponent (Ozaki et
+ * al., 2012); the slice products of equal order add up exactly in FP32 TMEM
+ * accumulators (K * slices <= 1024) and are combined in FP64 (slices = 7: about
+ * 49 significant bits of the row and column scales).  The paper's column
+ * steps (Fig. 1(c); Fig. "contraction", Step 4) are such contractions; this
+ * entry point measures the tensor-core form of them against peps_cc_gemm.
+ *   workspace: device, 256-byte aligned, peps_tc_workspace_bytes() bytes
+ *   (the slice images and exponents); status: device int32, bit 1 / 2 set
+ *   when a bounded wait on the copies / MMAs ran out (C not written).
+ * 1 <= slices <= 8.  Asynchronous on `stream`. */
+size_t peps_tc_workspace_bytes(int32_t M, int32_t N, int32_t K, int64_t batch,
+                               int32_t slices, int32_t b_shared);
+int peps_tc_gemm(const double* A, const double* B, double* C, int32_t M,
+                 int32_t N, int32_t K, int64_t batch, int32_t b_shared,
+                 int32_t slices, void* workspace, size_t workspace_bytes,
+                 int32_t* status, void* stream);
+
+/* The same batched contraction on the CUDA cores with the persistent kernels'
+ * contract() routine in the arithmetic of `precision` (PEPS_FP64, PEPS_MIXED
+ * float-float, PEPS_FP32), one thread block per batch element.  convert = 1:
+ * A and B are converted into the workspace and C converted back; convert = 0
+ * runs the contraction alone on operands an earlier call converted (for
+ * timing).  workspace: peps_cc_workspace_bytes() bytes, device. */
+size_t peps_cc_workspace_bytes(int32_t precision, int32_t M, int32_t N, int32_t K,
+                               int64_t batch, int32_t b_shared);
+int peps_cc_gemm(int32_t precision, const double* A, const double* B, double* C,
+                 int32_t M, int32_t N, int32_t K, int64_t batch, int32_t b_shared,
+                 void* workspace, size_t workspace_bytes, int32_t convert, void* stream);
+
 /* Wait for `stream` and return the device-side error state: PEPS_OK, or
  * PEPS_ENUMERIC with *flags (host, nullable) set to the PEPS_FLAG_* bits
  * seen since the last call (the bits are cleared). */

@@ -26,8 +26,11 @@ def bond_count(L):
     return 2 * L * (L - 1) + 2 * (L - 1) ** 2
 
 
+_PREC = {"fp64": PEPS_FP64, "mixed": PEPS_MIXED, "fp32": PEPS_FP32}
+
+
 def _shape(L, D, Dc, J1, J2, precision):
-    prec = {"fp64": PEPS_FP64, "mixed": PEPS_MIXED, "fp32": PEPS_FP32}.get(precision, precision)
+    prec = _PREC.get(precision, precision)
     return PepsShape(int(L), int(D), int(Dc), float(J1), float(J2), int(prec))
 
 
@@ -292,3 +295,52 @@ class PepsServer:
             self.close()
         except Exception:
             pass
+
+
+class Contraction:
+    """Batched C_b = A_b B_b (float64 device tensors [batch, M, K] and
+    [batch or 1, K, N]) on the tensor cores (tcgen05, error-free BF16 slices:
+    peps_tc_gemm) or on the CUDA cores (contract(): peps_cc_gemm), with the
+    workspace held between calls so that repeated calls time the kernels."""
+
+    def __init__(self, M, N, K, batch, b_shared=False, slices=7):
+        import torch
+        self.torch = torch
+        self.lib = _lib.load()
+        self.M, self.N, self.K, self.batch = int(M), int(N), int(K), int(batch)
+        self.b_shared = int(bool(b_shared))
+        self.slices = int(slices)
+        nb = self.lib.peps_tc_workspace_bytes(self.M, self.N, self.K, self.batch, self.slices,
+                                              self.b_shared)
+        if nb == 0:
+            raise PepsError(_lib.PEPS_EINVAL, "shape not supported by peps_tc_gemm")
+        self.ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        self.status = torch.zeros(1, dtype=torch.int32, device="cuda")
+        self._cc = {}
+
+    def _stream(self):
+        return ctypes.c_void_p(self.torch.cuda.current_stream().cuda_stream)
+
+    def tensor_cores(self, A, B, C=None):
+        t = self.torch
+        C = C if C is not None else t.empty(self.batch, self.M, self.N, dtype=t.float64, device="cuda")
+        rc = self.lib.peps_tc_gemm(_ptr(A), _ptr(B), _ptr(C), self.M, self.N, self.K, self.batch,
+                                   self.b_shared, self.slices, _ptr(self.ws), self.ws.numel(),
+                                   _ptr(self.status), self._stream())
+        if rc != 0:
+            raise PepsError(rc, "peps_tc_gemm failed")
+        return C
+
+    def cuda_cores(self, A, B, precision="mixed", C=None, convert=True):
+        t = self.torch
+        prec = _PREC[precision]
+        if precision not in self._cc:
+            nb = self.lib.peps_cc_workspace_bytes(prec, self.M, self.N, self.K, self.batch, self.b_shared)
+            self._cc[precision] = t.empty(nb, dtype=t.uint8, device="cuda")
+        w = self._cc[precision]
+        C = C if C is not None else t.empty(self.batch, self.M, self.N, dtype=t.float64, device="cuda")
+        rc = self.lib.peps_cc_gemm(prec, _ptr(A), _ptr(B), _ptr(C), self.M, self.N, self.K, self.batch,
+                                   self.b_shared, _ptr(w), w.numel(), int(bool(convert)), self._stream())
+        if rc != 0:
+            raise PepsError(rc, "peps_cc_gemm failed")
+        return C

@@ -28,7 +28,8 @@ EXPORTS = ("peps_create", "peps_destroy", "peps_last_error", "peps_workspace_byt
            "peps_evaluate", "peps_grad_step", "peps_sample_batch", "peps_sync_status",
            "peps_flops_per_sample", "peps_amplitudes_noalloc", "peps_vmc_step",
            "peps_server_create", "peps_server_submit", "peps_server_wait", "peps_server_destroy",
-           "peps_correlations", "peps_structure_factor")
+           "peps_correlations", "peps_structure_factor", "peps_tc_workspace_bytes", "peps_tc_gemm",
+           "peps_cc_workspace_bytes", "peps_cc_gemm")
 
 
 class PepsShape(ctypes.Structure):
@@ -82,6 +83,10 @@ _SIGS = {
     "peps_server_destroy": (I32, [P]),
     "peps_correlations": (I32, [P, P, I64, I32, P, P, P, P]),
     "peps_structure_factor": (I32, [P, P, I32, P, F64, F64, P, P]),
+    "peps_tc_workspace_bytes": (ctypes.c_size_t, [I32, I32, I32, I64, I32, I32]),
+    "peps_tc_gemm": (I32, [P, P, P, I32, I32, I32, I64, I32, I32, P, ctypes.c_size_t, P, P]),
+    "peps_cc_workspace_bytes": (ctypes.c_size_t, [I32, I32, I32, I32, I64, I32]),
+    "peps_cc_gemm": (I32, [I32, P, P, P, I32, I32, I32, I64, I32, P, ctypes.c_size_t, I32, P]),
 }
 
 
