@@ -2,6 +2,8 @@
 contract's keys, and the serving benchmark's arrival stream is seeded."""
 import json
 import os
+
+import numpy as np
 import subprocess
 import sys
 
@@ -33,7 +35,16 @@ def test_serving_stream_is_seeded_and_follows_the_mix():
     assert a == b and len(a) > 10
     times = [x[0] for x in a]
     assert times == sorted(times) and times[-1] <= 20.0
-    shapes = {(L, D, Dc) for (L, D, Dc, _) in bench.SERVING_MIX}
+    shapes = set(bench.SERVING_SHAPES)
     for (_, L, D, Dc, B, _) in a:
-        assert (L, D, Dc) in shapes and Dc == 4 * D and B in (64, 128, 256)
+        assert (L, D, Dc) in shapes and Dc == 4 * D and B in bench.SERVING_SAMPLES
     assert bench.serving_stream(1235, 2.0, 20.0) != a
+    # the mix of the serving workload: every L in {8..24} with D in {4, 6, 8},
+    # Dc = 4 D, 64 to 1024 samples, weights summing to one
+    assert {L for L, _, _ in bench.SERVING_SHAPES} == {8, 12, 16, 20, 24}
+    assert {D for _, D, _ in bench.SERVING_SHAPES} == {4, 6, 8}
+    assert min(bench.SERVING_SAMPLES) == 64 and max(bench.SERVING_SAMPLES) == 1024
+    w = bench.serving_weights()
+    assert abs(w.sum() - 1.0) < 1e-12 and np.all(w > 0)
+    long = bench.serving_stream(7, 50.0, 200.0)
+    assert len({(L, D) for (_, L, D, _, _, _) in long}) >= 9
