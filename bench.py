@@ -322,10 +322,11 @@ CONTRACTIONS = [(3456, 36, 36), (864, 144, 24), (864, 24, 144)]
 def run_contraction(args):
     """--mode contraction: each column-step shape, batch = one contraction per
     slot of the persistent kernel, on the tensor cores (peps_tc_gemm: split +
-    MMA) and on the CUDA cores (peps_cc_gemm: contract() in float-float and in
-    FP64, operands converted beforehand); device time per batch (CUDA events,
-    mean of --steps after --warmup) and the worst error against the FP64
-    product relative to sum |a||b| on 4 batch elements."""
+    MMA, output in float-float and in FP64) and on the CUDA cores
+    (peps_cc_gemm: contract() in float-float and in FP64, operands converted
+    beforehand, output left in the form); device time per batch (CUDA
+    events, mean of --steps after --warmup) and the worst error against the
+    FP64 product relative to sum |a||b| on 4 batch elements."""
     import torch
 
     import paper_1806_03761_gb300 as P
@@ -342,11 +343,13 @@ def run_contraction(args):
         exact = np.einsum("bmk,bkn->bmn", An, Bn)
         scale = np.einsum("bmk,bkn->bmn", np.abs(An), np.abs(Bn))
         res = {"M": M, "N": N, "K": K, "batch": batch}
-        for name, fn in (("tensor_cores", lambda: c.tensor_cores(A, Bm, C)),
+        for name, fn in (("tensor_cores_ff_out", lambda: c.tensor_cores(A, Bm, Cf, out="mixed")),
+                         ("tensor_cores_fp64_out", lambda: c.tensor_cores(A, Bm, C)),
                          ("cuda_cores_ff", lambda: c.cuda_cores(A, Bm, "mixed", C, convert=False)),
                          ("cuda_cores_fp64", lambda: c.cuda_cores(A, Bm, "fp64", C, convert=False))):
             C = torch.empty(batch, M, N, dtype=torch.float64, device="cuda")
-            if name != "tensor_cores":  # operands converted once, outside the timing
+            Cf = torch.empty(batch, M, N, 2, dtype=torch.float32, device="cuda")
+            if name.startswith("cuda"):  # operands converted once, outside the timing
                 c.cuda_cores(A, Bm, "mixed" if name.endswith("ff") else "fp64", C, convert=True)
             for _ in range(args.warmup):
                 fn()
@@ -358,12 +361,14 @@ def run_contraction(args):
             t1.record(stream)
             torch.cuda.synchronize()
             ms = t0.elapsed_time(t1) / max(args.steps, 1)
-            if name != "tensor_cores":
+            if name.startswith("cuda"):
                 c.cuda_cores(A, Bm, "mixed" if name.endswith("ff") else "fp64", C, convert=True)
             else:
                 fn()
             torch.cuda.synchronize()
-            err = float(np.max(np.abs(C[:4].cpu().numpy() - exact) / scale))
+            got = C[:4].cpu().numpy() if name != "tensor_cores_ff_out" else \
+                Cf[:4].cpu().numpy().astype(np.float64).sum(axis=-1)
+            err = float(np.max(np.abs(got - exact) / scale))
             res[name] = {"ms": ms, "tflops": 2.0 * M * N * K * batch / (ms / 1e3) / 1e12, "err": err}
         res["status"] = int(c.status.item())
         rows.append(res)

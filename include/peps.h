@@ -260,8 +260,11 @@ int peps_structure_factor(peps_ctx* ctx, const double* ss_mean, int32_t n_src,
  * FP64-class accuracy: every row of A and column of B is split error-free
  * into `slices` BF16 integer slices of 7 bits at a common exponent (Ozaki et
  * al., 2012); the slice products of equal order add up exactly in FP32 TMEM
- * accumulators (K * slices <= 1024) and are combined in FP64 (slices = 7: about
- * 49 significant bits of the row and column scales).  The paper's column
+ * accumulators (K * slices <= 1024) and are combined exactly into FP64
+ * (c_format = PEPS_FP64: C is float64[M][N]) or into float-float
+ * (c_format = PEPS_MIXED: C holds (hi, lo) FP32 pairs, the persistent
+ * kernels' form); slices = 7 keeps about 49 significant bits of the row and
+ * column scales.  One CTA per SM walks the tiles, holding its TMEM columns.  The paper's column
  * steps (Fig. 1(c); Fig. "contraction", Step 4) are such contractions; this
  * entry point measures the tensor-core form of them against peps_cc_gemm.
  *   workspace: device, 256-byte aligned, peps_tc_workspace_bytes() bytes
@@ -270,10 +273,10 @@ int peps_structure_factor(peps_ctx* ctx, const double* ss_mean, int32_t n_src,
  * 1 <= slices <= 8.  Asynchronous on `stream`. */
 size_t peps_tc_workspace_bytes(int32_t M, int32_t N, int32_t K, int64_t batch,
                                int32_t slices, int32_t b_shared);
-int peps_tc_gemm(const double* A, const double* B, double* C, int32_t M,
+int peps_tc_gemm(const double* A, const double* B, void* C, int32_t M,
                  int32_t N, int32_t K, int64_t batch, int32_t b_shared,
-                 int32_t slices, void* workspace, size_t workspace_bytes,
-                 int32_t* status, void* stream);
+                 int32_t slices, int32_t c_format, void* workspace,
+                 size_t workspace_bytes, int32_t* status, void* stream);
 
 /* The same batched contraction on the CUDA cores with the persistent kernels'
  * contract() routine in the arithmetic of `precision` (PEPS_FP64, PEPS_MIXED

@@ -321,12 +321,16 @@ class Contraction:
     def _stream(self):
         return ctypes.c_void_p(self.torch.cuda.current_stream().cuda_stream)
 
-    def tensor_cores(self, A, B, C=None):
+    def tensor_cores(self, A, B, C=None, out="fp64"):
+        """out = "fp64": C float64 [batch, M, N]; out = "mixed": C as
+        float-float pairs, a float32 tensor [batch, M, N, 2] (hi, lo)."""
         t = self.torch
-        C = C if C is not None else t.empty(self.batch, self.M, self.N, dtype=t.float64, device="cuda")
+        if C is None:
+            C = (t.empty(self.batch, self.M, self.N, dtype=t.float64, device="cuda") if out == "fp64"
+                 else t.empty(self.batch, self.M, self.N, 2, dtype=t.float32, device="cuda"))
         rc = self.lib.peps_tc_gemm(_ptr(A), _ptr(B), _ptr(C), self.M, self.N, self.K, self.batch,
-                                   self.b_shared, self.slices, _ptr(self.ws), self.ws.numel(),
-                                   _ptr(self.status), self._stream())
+                                   self.b_shared, self.slices, _PREC[out], _ptr(self.ws),
+                                   self.ws.numel(), _ptr(self.status), self._stream())
         if rc != 0:
             raise PepsError(rc, "peps_tc_gemm failed")
         return C

@@ -84,7 +84,7 @@ _SIGS = {
     "peps_correlations": (I32, [P, P, I64, I32, P, P, P, P]),
     "peps_structure_factor": (I32, [P, P, I32, P, F64, F64, P, P]),
     "peps_tc_workspace_bytes": (ctypes.c_size_t, [I32, I32, I32, I64, I32, I32]),
-    "peps_tc_gemm": (I32, [P, P, P, I32, I32, I32, I64, I32, I32, P, ctypes.c_size_t, P, P]),
+    "peps_tc_gemm": (I32, [P, P, P, I32, I32, I32, I64, I32, I32, I32, P, ctypes.c_size_t, P, P]),
     "peps_cc_workspace_bytes": (ctypes.c_size_t, [I32, I32, I32, I32, I64, I32]),
     "peps_cc_gemm": (I32, [I32, P, P, P, I32, I32, I32, I64, I32, P, ctypes.c_size_t, I32, P]),
 }

@@ -7,8 +7,9 @@
 //
 // Error-free splitting (Ozaki, Ogita, Oishi and Rump, Numer. Algorithms 59,
 // 2012).  Row i of A is scaled by 2^-e_i (e_i: the exponent of its largest
-// entry) and cut into s slices, slice t holding the integer
-// q_t = rint(r_t 2^(7(t+1))) of the running remainder r_t (|q_t| <= 128, exact
+// entry) and cut into s slices of 7 bits: slice t holds the signed digit
+// q_t in [-127, 127] of |x| 2^-e_i = sum_t |q_t| 2^-7(t+1) + (a remainder
+// below 2^-7s), read off the bits of x with integer operations only (exact
 // in BF16); column j of B likewise with f_j.  A product of slices t_a and t_b
 // is an integer multiple of 2^-7(t_a+t_b+2) of magnitude < 2^14, so the K
 // products of every pair with the same g = t_a + t_b (at most s pairs) add up
@@ -93,13 +94,22 @@ __global__ void tc_split_kernel(const double* X, int64_t sb, int64_t rs, int64_t
     const int64_t blk = (int64_t)tile_rows * TC_KC;
     __nv_bfloat16* base = img + ((b * n_tiles + T) * (int64_t)s) * nch * blk;
     for (int k = lane; k < Kp; k += 32) {
-      double rem = (r < rows && k < K) ? ldexp(x[(int64_t)k * cs], -e) : 0.0;
+      const double xv = (r < rows && k < K) ? x[(int64_t)k * cs] : 0.0;
+      // |x| 2^(62-e) truncated to an integer, from the bits of x: no FP64
+      // arithmetic (the mantissa shifted by the exponent difference)
+      const unsigned long long bits = (unsigned long long)__double_as_longlong(xv);
+      const int ex = (int)((bits >> 52) & 0x7FF);
+      const unsigned long long mant = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+      const int sh = ex - 1075 + 62 - e;  // |x| = mant 2^(ex-1075) < 2^e
+      unsigned long long mag = 0;
+      if (ex != 0) mag = sh >= 0 ? (mant << sh) : (-sh < 64 ? (mant >> -sh) : 0ull);
+      const bool neg = (bits >> 63) != 0;
       const int64_t off = (k / TC_KC) * blk + tc_core_off(rr, k % TC_KC) / 2;
       for (int t = 0; t < s; ++t) {
-        const double sc = ldexp(1.0, TC_SLICE_BITS * (t + 1));
-        const double q = rint(rem * sc);           // |q| <= 128: exact in BF16
-        rem -= q / sc;                              // exact (same grid)
-        base[(int64_t)t * nch * blk + off] = __float2bfloat16_rn((float)q);
+        // digit t: bits 61-7t .. 55-7t, i.e. |x| 2^-e = sum_t d_t 2^-7(t+1)
+        // + (below 2^-7s), d_t in [0, 127], exact in BF16
+        const int d = (int)((mag >> (55 - TC_SLICE_BITS * t)) & 0x7F);
+        base[(int64_t)t * nch * blk + off] = __float2bfloat16_rn((float)(neg ? -d : d));
       }
     }
   }
@@ -182,6 +192,8 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
                    smem_addr(bar))
                : "memory");
 }
+// 32 lanes x 16 columns of 32 bits from TMEM; the values may be read only
+// after tmem_wait()
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   uint32_t r[16];
   asm volatile(
@@ -191,9 +203,11 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
         "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
         "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+}
+__device__ __forceinline__ void tmem_wait() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -204,18 +218,31 @@ struct TcArgs {
   const __nv_bfloat16* bimg;  // [batch or 1][s][Kp / TC_KC][Np][TC_KC]
   const int* ea;              // [batch][Mp]
   const int* eb;              // [batch or 1][Np]
-  double* C;                  // element (i, j) of batch b at C[b*sc + i*ldc + j]
+  void* C;                    // element (i, j) of batch b at C[b*sc + i*ldc + j] (double or ff)
   int64_t sc, ldc;
   int M, N, Kp, Mp, Np, ntile, s;
+  int64_t batch;
   int b_shared;               // B (and its image) shared by the batch
   int* status;                // error bits: 1 copy wait, 2 MMA wait ran out
 };
 
+// 2^k as FP32 / FP64 from the exponent bits (exact; k in the normal range)
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) << 23); }
+__device__ __forceinline__ double pow2d(int k) {
+  return __longlong_as_double((long long)(1023 + k) << 52);
+}
+
+// Persistent: each CTA walks the (batch, row tile, column tile) tiles with a
+// stride of the grid, holding its TMEM columns throughout; the next tile's
+// first chunk is copied while the current tile's accumulators are read out.
+// FF: write C as float-float (hi, lo), the form the persistent kernels use;
+// else FP64.
+template <bool FF>
 __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  const int mt = blockIdx.x, nt = blockIdx.y;
-  const int64_t b = blockIdx.z;
   const int s = a.s, ntile = a.ntile, nch = a.Kp / TC_KC;
+  const int m_tiles = a.Mp / TC_ROWS, n_tiles = a.Np / ntile;
+  const int64_t tiles = a.batch * m_tiles * n_tiles;
   const uint32_t a_blk = (uint32_t)TC_ROWS * TC_KC * 2;   // one slice, one chunk
   const uint32_t b_blk = (uint32_t)ntile * TC_KC * 2;
   unsigned char* sa = smem;
@@ -240,69 +267,107 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(TcArgs a) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
-  const int64_t bb = a.b_shared ? 0 : b;
-  const __nv_bfloat16* ga = a.aimg + ((b * (a.Mp / TC_ROWS) + mt) * (int64_t)s) * nch * (TC_ROWS * TC_KC);
-  const __nv_bfloat16* gb = a.bimg + (bb * (int64_t)s) * nch * ((int64_t)a.Np * TC_KC) +
-                            (int64_t)nt * ntile * TC_KC;
   const uint32_t idesc = umma_idesc(TC_ROWS, ntile);
   const uint32_t sbo = (uint32_t)(TC_KC / 8) * 128;
+  // thread 0: the bulk copies of chunk c of tile `tl`
+  auto issue_copy = [&](int64_t tl, int c) {
+    const int nt = (int)(tl % n_tiles);
+    const int mt = (int)((tl / n_tiles) % m_tiles);
+    const int64_t b = tl / ((int64_t)n_tiles * m_tiles);
+    const int64_t bb = a.b_shared ? 0 : b;
+    const __nv_bfloat16* ga = a.aimg + ((b * m_tiles + mt) * (int64_t)s) * nch * (TC_ROWS * TC_KC);
+    const __nv_bfloat16* gb = a.bimg + (bb * (int64_t)s) * nch * ((int64_t)a.Np * TC_KC) +
+                              (int64_t)nt * ntile * TC_KC;
+    mbar_expect_tx(bar, (uint32_t)s * (a_blk + b_blk));
+    for (int t = 0; t < s; ++t) {
+      bulk_g2s(sa + (size_t)t * a_blk, ga + ((int64_t)t * nch + c) * (TC_ROWS * TC_KC), a_blk, bar);
+      bulk_g2s(sb + (size_t)t * b_blk, gb + ((int64_t)t * nch + c) * ((int64_t)a.Np * TC_KC), b_blk, bar);
+    }
+  };
   uint32_t phase = 0;
   int err = 0;  // 1: a copy wait ran out, 2: an MMA wait ran out
-  for (int c = 0; c < nch && !err; ++c) {
-    // 1. chunk c of every slice of A and B into shared memory (the previous
-    //    chunk's MMAs have completed: its commit phase was waited for)
-    if (threadIdx.x == 0) {
-      mbar_expect_tx(bar, (uint32_t)s * (a_blk + b_blk));
-      for (int t = 0; t < s; ++t) {
-        bulk_g2s(sa + (size_t)t * a_blk, ga + ((int64_t)t * nch + c) * (TC_ROWS * TC_KC), a_blk, bar);
-        bulk_g2s(sb + (size_t)t * b_blk, gb + ((int64_t)t * nch + c) * ((int64_t)a.Np * TC_KC), b_blk, bar);
-      }
-    }
-    if (!__syncthreads_and(mbar_wait(bar, phase & 1))) { err = 1; break; }
-    ++phase;
-    // 2. the MMAs of chunk c: accumulator g collects the slice pairs with
-    //    t_a + t_b = g; the first MMA into each accumulator overwrites it
-    if (threadIdx.x == 0) {
-      tc_fence_after();
-      for (int g = 0; g < s; ++g)
-        for (int ta = 0; ta <= g; ++ta) {
-          const int tb = g - ta;
-          for (int kk = 0; kk < TC_KC / 16; ++kk) {
-            const uint64_t da = umma_desc(smem_addr(sa + (size_t)ta * a_blk + kk * 256), 128, sbo);
-            const uint64_t db = umma_desc(smem_addr(sb + (size_t)tb * b_blk + kk * 256), 128, sbo);
-            umma_bf16(tmem + (uint32_t)(g * ntile), da, db, idesc, (c | ta | kk) ? 1u : 0u);
+  if (threadIdx.x == 0 && (int64_t)blockIdx.x < tiles) issue_copy(blockIdx.x, 0);
+  for (int64_t tl = blockIdx.x; tl < tiles && !err; tl += gridDim.x) {
+    for (int c = 0; c < nch; ++c) {
+      if (c > 0 && threadIdx.x == 0) issue_copy(tl, c);  // chunk 0 was prefetched
+      if (!__syncthreads_and(mbar_wait(bar, phase & 1))) { err = 1; break; }
+      ++phase;
+      // the MMAs of chunk c: accumulator g collects the slice pairs with
+      // t_a + t_b = g; the first MMA into each accumulator overwrites it
+      if (threadIdx.x == 0) {
+        tc_fence_after();
+        for (int g = 0; g < s; ++g)
+          for (int ta = 0; ta <= g; ++ta) {
+            const int tb = g - ta;
+            for (int kk = 0; kk < TC_KC / 16; ++kk) {
+              const uint64_t da = umma_desc(smem_addr(sa + (size_t)ta * a_blk + kk * 256), 128, sbo);
+              const uint64_t db = umma_desc(smem_addr(sb + (size_t)tb * b_blk + kk * 256), 128, sbo);
+              umma_bf16(tmem + (uint32_t)(g * ntile), da, db, idesc, (c | ta | kk) ? 1u : 0u);
+            }
           }
-        }
-      umma_commit(bar);
+        umma_commit(bar);
+      }
+      if (!__syncthreads_and(mbar_wait(bar, phase & 1))) { err = 2; break; }
+      ++phase;
     }
-    if (!__syncthreads_and(mbar_wait(bar, phase & 1))) { err = 2; break; }
-    ++phase;
-  }
-  tc_fence_after();
-  // 3. epilogue: row i = 32 warp + lane of the tile, FP64 combination
-  const int i = mt * TC_ROWS + warp * 32 + lane;
-  if (!err) {
+    if (err) break;
+    // the shared buffers are free: prefetch the next tile's first chunk
+    if (threadIdx.x == 0 && tl + gridDim.x < tiles) issue_copy(tl + gridDim.x, 0);
+    tc_fence_after();
+    // epilogue: row i = 32 warp + lane of the tile
+    const int nt = (int)(tl % n_tiles);
+    const int mt = (int)((tl / n_tiles) % m_tiles);
+    const int64_t b = tl / ((int64_t)n_tiles * m_tiles);
+    const int64_t bb = a.b_shared ? 0 : b;
+    const int i = mt * TC_ROWS + warp * 32 + lane;
     const int ei = a.ea[b * a.Mp + i];
     for (int j0 = 0; j0 < ntile; j0 += 16) {
-      double accd[16];
+      float v[8][16];
 #pragma unroll
-      for (int q = 0; q < 16; ++q) accd[q] = 0.0;
-      for (int g = s - 1; g >= 0; --g) {
-        float v[16];
-        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(g * ntile + j0), v);
-        const double w = ldexp(1.0, -TC_SLICE_BITS * (g + 2));
-#pragma unroll
-        for (int q = 0; q < 16; ++q) accd[q] += (double)v[q] * w;
-      }
+      for (int g = 0; g < 8; ++g)
+        if (g < s) tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(g * ntile + j0), v[g]);
+      tmem_wait();
       if (i < a.M) {
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
           const int j = nt * ntile + j0 + q;
-          if (j < a.N) a.C[b * a.sc + (int64_t)i * a.ldc + j] = ldexp(accd[q], ei + a.eb[bb * a.Np + j]);
+          if (j >= a.N) continue;
+          const int sc = ei + a.eb[bb * a.Np + j];
+          const int64_t at = b * a.sc + (int64_t)i * a.ldc + j;
+          if (FF) {
+            // sum_g acc_g 2^-7(g+2), smallest first, in float-float (every
+            // term exact in FP32), then the row/column scale
+            ff acc = {0.0f, 0.0f};
+#pragma unroll
+            for (int g = 7; g >= 0; --g)
+              if (g < s) {
+                const ff t = ff_two_sum(acc.hi, v[g][q] * pow2f(-TC_SLICE_BITS * (g + 2)));
+                acc = ff_fast_two_sum(t.hi, __fadd_rn(acc.lo, t.lo));
+              }
+            const float p2 = pow2f(sc);
+            static_cast<ff*>(a.C)[at] = ff{acc.hi * p2, acc.lo * p2};
+          } else {
+            // exact integer combination in two parts (|acc_g| < 2^24), one
+            // rounding: sum_g acc_g 2^-7(g+2) = H 2^-28 + Lo 2^-56
+            long long H = 0, Lo = 0;
+#pragma unroll
+            for (int g = 0; g < 8; ++g)
+              if (g < s) {
+                const long long x = (long long)__float2int_rn(v[g][q]);
+                if (g < 3) H += x << (TC_SLICE_BITS * (2 - g));
+                else Lo += x << (TC_SLICE_BITS * (6 - g));
+              }
+            const double val = fma((double)H, pow2d(-28), (double)Lo * pow2d(-56));
+            static_cast<double*>(a.C)[at] = val * pow2d(sc);
+          }
         }
       }
     }
-  } else if (threadIdx.x == 0) {
+    tc_fence_before();
+    __syncthreads();  // every TMEM read done before the next tile's MMAs
+    tc_fence_after();
+  }
+  if (err && threadIdx.x == 0) {
     atomicOr(a.status, err);
     // let the copies or the MMAs in flight finish, within the same bound,
     // before the shared memory and the TMEM columns are released
@@ -380,11 +445,12 @@ size_t peps_tc_workspace_bytes(int32_t M, int32_t N, int32_t K, int64_t batch, i
   return L.total;
 }
 
-int peps_tc_gemm(const double* A, const double* B, double* C, int32_t M, int32_t N, int32_t K,
-                 int64_t batch, int32_t b_shared, int32_t slices, void* workspace,
+int peps_tc_gemm(const double* A, const double* B, void* C, int32_t M, int32_t N, int32_t K,
+                 int64_t batch, int32_t b_shared, int32_t slices, int32_t c_format, void* workspace,
                  size_t workspace_bytes, int32_t* status, void* stream) {
   TcLayout L;
   if (!A || !B || !C || !workspace || !status) return PEPS_EINVAL;
+  if (c_format != PEPS_FP64 && c_format != PEPS_MIXED) return PEPS_EINVAL;
   if (!tc_layout(M, N, K, batch, slices, b_shared, &L)) return PEPS_EINVAL;
   if (workspace_bytes < L.total) return PEPS_EINVAL;
   if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0) return PEPS_EINVAL;
@@ -402,8 +468,13 @@ int peps_tc_gemm(const double* A, const double* B, double* C, int32_t M, int32_t
   tc_split_kernel<<<grid_for(bb * L.Np), 256, 0, st>>>(B, (int64_t)K * N, 1, N, N, K, L.Np, L.Np,
                                                        L.Kp, slices, bb, bimg, eb);
   if (cudaGetLastError() != cudaSuccess) return PEPS_ECUDA;
-  if (cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem) !=
-      cudaSuccess)
+  const bool ffout = c_format == PEPS_MIXED;
+  if (cudaFuncSetAttribute(ffout ? tc_gemm_kernel<true> : tc_gemm_kernel<false>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem) != cudaSuccess)
+    return PEPS_ECUDA;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return PEPS_ECUDA;
   TcArgs a;
   a.aimg = aimg;
@@ -414,10 +485,13 @@ int peps_tc_gemm(const double* A, const double* B, double* C, int32_t M, int32_t
   a.sc = (int64_t)M * N;
   a.ldc = N;
   a.M = M; a.N = N; a.Kp = L.Kp; a.Mp = L.Mp; a.Np = L.Np; a.ntile = L.ntile; a.s = slices;
+  a.batch = batch;
   a.b_shared = b_shared;
   a.status = status;
-  dim3 grid(L.m_tiles, L.n_tiles, (unsigned)batch);
-  tc_gemm_kernel<<<grid, 128, L.smem, st>>>(a);
+  const int64_t tiles = batch * L.m_tiles * L.n_tiles;
+  const int grid = (int)std::min<int64_t>(tiles, sms);  // one CTA per SM (TMEM, shared memory)
+  if (ffout) tc_gemm_kernel<true><<<grid, 128, L.smem, st>>>(a);
+  else tc_gemm_kernel<false><<<grid, 128, L.smem, st>>>(a);
   return cudaGetLastError() == cudaSuccess ? PEPS_OK : PEPS_ECUDA;
 }
 
