@@ -290,6 +290,43 @@ int peps_cc_gemm(int32_t precision, const double* A, const double* B, double* C,
                  int32_t M, int32_t N, int32_t K, int64_t batch, int32_t b_shared,
                  void* workspace, size_t workspace_bytes, int32_t convert, void* stream);
 
+/* Several jobs of different lattice sizes and bond dimensions (one precision
+ * form) in ONE persistent launch: the local energies of every job's samples
+ * (Eq. ess), computed exactly as peps_local_energy computes them.  A pool
+ * holds the slot workspaces (sized for the largest of `shapes`) and the
+ * work queue: the blocks claim (job, sample) items one at a time with an
+ * atomic counter, the costliest jobs' items first, so that items of very
+ * different cost share the SMs without waves.
+ *   peps_pool_create: precision PEPS_FP64 or PEPS_MIXED; slots (0: two per
+ *   SM); shapes: HOST array of the shapes the pool will run (their
+ *   precision must be the pool's); max_jobs: jobs per launch.
+ *   peps_multi_job: ctx (a context of the job's shape, tensors set; its own
+ *   workspace is not used), spins uint8[B][N] (device), outputs as in
+ *   peps_local_energy (e_loc required; log_abs, sign, ratios, n_flips
+ *   nullable).  Errors: PEPS_EINVAL for a shape larger than the pool's, a
+ *   context of another form or device, n_jobs > max_jobs.  Device-side
+ *   conditions collect in the pool's flags (peps_pool_sync_status).
+ * Calls on one pool are ordered on one stream (the queue counter and the
+ * job table are the pool's). */
+typedef struct peps_pool peps_pool;
+typedef struct {
+  peps_ctx* ctx;
+  const uint8_t* spins;
+  int64_t B;
+  double* e_loc;
+  double* log_abs;
+  int8_t* sign;
+  double* ratios;
+  int32_t* n_flips;
+} peps_multi_job;
+int peps_pool_create(int32_t precision, int32_t slots, const peps_shape* shapes,
+                     int32_t n_shapes, int32_t max_jobs, peps_pool** out);
+int peps_pool_destroy(peps_pool* pool);
+int peps_pool_slots(const peps_pool* pool, int32_t* slots);
+int peps_local_energy_multi(peps_pool* pool, const peps_multi_job* jobs, int32_t n_jobs,
+                            void* stream);
+int peps_pool_sync_status(peps_pool* pool, void* stream, int32_t* flags);
+
 /* Wait for `stream` and return the device-side error state: PEPS_OK, or
  * PEPS_ENUMERIC with *flags (host, nullable) set to the PEPS_FLAG_* bits
  * seen since the last call (the bits are cleared). */

@@ -297,6 +297,65 @@ class PepsServer:
             pass
 
 
+class PepsPool:
+    """Jobs of different shapes in one persistent launch (peps_local_energy_multi):
+    a slot pool sized for the largest of `shapes` ((L, D, Dc) tuples), one
+    precision form.  local_energy(jobs) takes [(PepsContext, spins), ...] and
+    returns one dict per job (e_loc, log_abs, sign, ratios, n_flips)."""
+
+    def __init__(self, shapes, precision="mixed", slots=0, max_jobs=64, J1=1.0, J2=0.5):
+        import torch
+        self.torch = torch
+        self.lib = _lib.load()
+        arr = (PepsShape * len(shapes))(*[_shape(L, D, Dc, J1, J2, precision) for (L, D, Dc) in shapes])
+        h = ctypes.c_void_p()
+        rc = self.lib.peps_pool_create(_PREC[precision], int(slots), arr, len(shapes), int(max_jobs),
+                                       ctypes.byref(h))
+        if rc != 0:
+            raise PepsError(rc, "peps_pool_create failed")
+        self.h = h
+        n = ctypes.c_int32(0)
+        self.lib.peps_pool_slots(self.h, ctypes.byref(n))
+        self.slots = n.value
+
+    def local_energy(self, jobs, ratios=False, n_flips=False):
+        t = self.torch
+        outs, arr = [], (_lib.PepsMultiJob * len(jobs))()
+        for q, (ctx, spins) in enumerate(jobs):
+            s = ctx._spins(spins)
+            B = s.shape[0]
+            o = dict(e_loc=ctx._empty(B), log_abs=ctx._empty(B), sign=ctx._empty(B, dtype=t.int8),
+                     ratios=ctx._empty(B, ctx.nbonds) if ratios else None,
+                     n_flips=ctx._empty(B, dtype=t.int32) if n_flips else None)
+            outs.append(o)
+            arr[q] = _lib.PepsMultiJob(ctx.h, s.data_ptr(), B, o["e_loc"].data_ptr(),
+                                       o["log_abs"].data_ptr(), o["sign"].data_ptr(),
+                                       o["ratios"].data_ptr() if ratios else None,
+                                       o["n_flips"].data_ptr() if n_flips else None)
+        stream = ctypes.c_void_p(t.cuda.current_stream().cuda_stream)
+        rc = self.lib.peps_local_energy_multi(self.h, arr, len(jobs), stream)
+        if rc != 0:
+            raise PepsError(rc, "peps_local_energy_multi failed")
+        return outs
+
+    def sync_status(self):
+        f = ctypes.c_int32(0)
+        rc = self.lib.peps_pool_sync_status(self.h, ctypes.c_void_p(
+            self.torch.cuda.current_stream().cuda_stream), ctypes.byref(f))
+        return rc, f.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.peps_pool_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Contraction:
     """Batched C_b = A_b B_b (float64 device tensors [batch, M, K] and
     [batch or 1, K, N]) on the tensor cores (tcgen05, error-free BF16 slices:

@@ -29,7 +29,8 @@ EXPORTS = ("peps_create", "peps_destroy", "peps_last_error", "peps_workspace_byt
            "peps_flops_per_sample", "peps_amplitudes_noalloc", "peps_vmc_step",
            "peps_server_create", "peps_server_submit", "peps_server_wait", "peps_server_destroy",
            "peps_correlations", "peps_structure_factor", "peps_tc_workspace_bytes", "peps_tc_gemm",
-           "peps_cc_workspace_bytes", "peps_cc_gemm")
+           "peps_cc_workspace_bytes", "peps_cc_gemm", "peps_pool_create", "peps_pool_destroy",
+           "peps_pool_slots", "peps_local_energy_multi", "peps_pool_sync_status")
 
 
 class PepsShape(ctypes.Structure):
@@ -44,6 +45,12 @@ class PepsJob(ctypes.Structure):
     _fields_ = [("shape", PepsShape), ("A", ctypes.c_void_p), ("spins", ctypes.c_void_p),
                 ("B", ctypes.c_int64), ("e_loc", ctypes.c_void_p), ("log_abs", ctypes.c_void_p),
                 ("sign", ctypes.c_void_p)]
+
+
+class PepsMultiJob(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_void_p), ("spins", ctypes.c_void_p), ("B", ctypes.c_int64),
+                ("e_loc", ctypes.c_void_p), ("log_abs", ctypes.c_void_p), ("sign", ctypes.c_void_p),
+                ("ratios", ctypes.c_void_p), ("n_flips", ctypes.c_void_p)]
 
 
 class PepsJobStats(ctypes.Structure):
@@ -87,6 +94,11 @@ _SIGS = {
     "peps_tc_gemm": (I32, [P, P, P, I32, I32, I32, I64, I32, I32, I32, P, ctypes.c_size_t, P, P]),
     "peps_cc_workspace_bytes": (ctypes.c_size_t, [I32, I32, I32, I32, I64, I32]),
     "peps_cc_gemm": (I32, [I32, P, P, P, I32, I32, I32, I64, I32, P, ctypes.c_size_t, I32, P]),
+    "peps_pool_create": (I32, [I32, I32, ctypes.POINTER(PepsShape), I32, I32, ctypes.POINTER(P)]),
+    "peps_pool_destroy": (I32, [P]),
+    "peps_pool_slots": (I32, [P, ctypes.POINTER(I32)]),
+    "peps_local_energy_multi": (I32, [P, ctypes.POINTER(PepsMultiJob), I32, P]),
+    "peps_pool_sync_status": (I32, [P, P, ctypes.POINTER(I32)]),
 }
 
 

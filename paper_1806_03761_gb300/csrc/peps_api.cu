@@ -495,6 +495,170 @@ int peps_structure_factor(peps_ctx* c, const double* ss_mean, int32_t n_src, con
   return PEPS_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Multi-job launches (jobs of different shapes, one precision form).
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+struct peps_pool {
+  int precision = 0;
+  int nslots = 0;
+  int max_jobs = 0;
+  int device = 0;
+  int64_t slot_elems = 0, slot_doubles = 0;
+  void* ws = nullptr;
+  double* wsd = nullptr;
+  void* jobs = nullptr;               // MultiJobDev<R>[max_jobs]
+  unsigned long long* next = nullptr; // the work-queue counter
+  int* flags = nullptr;
+};
+
+namespace {
+
+template <class R>
+int launch_multi(peps_pool* pool, const peps_multi_job* jobs, int32_t n_jobs, cudaStream_t st) {
+  // the costliest jobs first (per-sample cost ~ L^3 (D Dc)^3), so that their
+  // long items start early and the cheap ones fill in behind them
+  std::vector<int> order(n_jobs);
+  for (int q = 0; q < n_jobs; ++q) order[q] = q;
+  auto cost = [&](int q) {
+    const PepsPlan& P = jobs[q].ctx->plan;
+    const double x = (double)P.D * P.Dc;
+    return (double)P.L * P.L * P.L * x * x * x;
+  };
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost(x) > cost(y); });
+  std::vector<MultiJobDev<R>> h(n_jobs);
+  int64_t items = 0;
+  for (int k = 0; k < n_jobs; ++k) {
+    const peps_multi_job& j = jobs[order[k]];
+    MultiJobDev<R>& d = h[k];
+    std::memset(&d, 0, sizeof(d));
+    d.a.P = j.ctx->plan;
+    d.a.steps = j.ctx->steps;
+    d.a.As = static_cast<const R*>(j.ctx->As);
+    d.a.spins = j.spins;
+    d.a.B = j.B;
+    d.a.want_energy = 1;
+    d.a.e_loc = j.e_loc;
+    d.a.log_abs = j.log_abs;
+    d.a.sign = j.sign;
+    d.a.ratios = j.ratios;
+    d.a.n_flips = j.n_flips;
+    d.a.flags = pool->flags;
+    d.first_item = items;
+    items += j.B;
+  }
+  if (items == 0) return PEPS_OK;
+  // pageable source: the call returns once the bytes are staged
+  if (cudaMemcpyAsync(pool->jobs, h.data(), h.size() * sizeof(MultiJobDev<R>), cudaMemcpyHostToDevice,
+                      st) != cudaSuccess ||
+      cudaMemsetAsync(pool->next, 0, sizeof(unsigned long long), st) != cudaSuccess)
+    return PEPS_ECUDA;
+  const int grid = (int)std::min<int64_t>(pool->nslots, items);
+  cudaError_t e;
+  if (pool->precision == PEPS_FP64)
+    e = peps_launch_multi_f64(static_cast<const MultiJobDev<double>*>(pool->jobs), n_jobs, items,
+                              pool->next, static_cast<double*>(pool->ws), pool->wsd,
+                              pool->slot_elems, pool->slot_doubles, pool->flags, grid, st);
+  else
+    e = peps_launch_multi_ff(static_cast<const MultiJobDev<ff>*>(pool->jobs), n_jobs, items,
+                             pool->next, static_cast<ff*>(pool->ws), pool->wsd, pool->slot_elems,
+                             pool->slot_doubles, pool->flags, grid, st);
+  return e == cudaSuccess ? PEPS_OK : PEPS_ECUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+int peps_pool_create(int32_t precision, int32_t slots, const peps_shape* shapes, int32_t n_shapes,
+                     int32_t max_jobs, peps_pool** out) {
+  if (!out) return PEPS_EINVAL;
+  *out = nullptr;
+  if (precision != PEPS_FP64 && precision != PEPS_MIXED) return PEPS_EINVAL;
+  if (!shapes || n_shapes < 1 || max_jobs < 1 || slots < 0) return PEPS_EINVAL;
+  int64_t se = 0, sd = 0;
+  for (int q = 0; q < n_shapes; ++q) {
+    std::string why;
+    if (!shape_ok(&shapes[q], &why) || shapes[q].precision != precision) return PEPS_EINVAL;
+    PepsPlan P;
+    std::vector<PepsStep> st;
+    make_plan(shapes[q], 1, &P, &st);
+    se = std::max(se, P.slot_elems);
+    sd = std::max(sd, P.slot_doubles);
+  }
+  peps_pool* p = new (std::nothrow) peps_pool();
+  if (!p) return PEPS_ENOMEM;
+  if (cudaGetDevice(&p->device) != cudaSuccess) { delete p; return PEPS_ECUDA; }
+  p->precision = precision;
+  p->nslots = slots > 0 ? slots : default_slots();
+  p->max_jobs = max_jobs;
+  p->slot_elems = se;
+  p->slot_doubles = sd;
+  const size_t es = elem_size(precision);
+  const size_t jb = precision == PEPS_FP64 ? sizeof(MultiJobDev<double>) : sizeof(MultiJobDev<ff>);
+  bool ok = p->nslots > 0 &&
+            cudaMalloc(&p->ws, (size_t)p->nslots * se * es) == cudaSuccess &&
+            cudaMalloc(&p->wsd, (size_t)p->nslots * sd * 8) == cudaSuccess &&
+            cudaMalloc(&p->jobs, (size_t)max_jobs * jb) == cudaSuccess &&
+            cudaMalloc(&p->next, sizeof(unsigned long long)) == cudaSuccess &&
+            cudaMalloc(&p->flags, sizeof(int)) == cudaSuccess;
+  if (!ok || cudaMemset(p->flags, 0, sizeof(int)) != cudaSuccess ||
+      cudaMemset(p->ws, 0, (size_t)p->nslots * se * es) != cudaSuccess) {
+    cudaGetLastError();
+    peps_pool_destroy(p);
+    return PEPS_ENOMEM;
+  }
+  *out = p;
+  return PEPS_OK;
+}
+
+int peps_pool_destroy(peps_pool* p) {
+  if (!p) return PEPS_EINVAL;
+  cudaFree(p->ws);
+  cudaFree(p->wsd);
+  cudaFree(p->jobs);
+  cudaFree(p->next);
+  cudaFree(p->flags);
+  delete p;
+  return PEPS_OK;
+}
+
+int peps_pool_slots(const peps_pool* p, int32_t* slots) {
+  if (!p || !slots) return PEPS_EINVAL;
+  *slots = p->nslots;
+  return PEPS_OK;
+}
+
+int peps_local_energy_multi(peps_pool* pool, const peps_multi_job* jobs, int32_t n_jobs,
+                            void* stream) {
+  if (!pool || !jobs || n_jobs < 1 || n_jobs > pool->max_jobs) return PEPS_EINVAL;
+  for (int q = 0; q < n_jobs; ++q) {
+    const peps_multi_job& j = jobs[q];
+    if (!j.ctx || !j.ctx->tensors_set || j.B < 0) return PEPS_EINVAL;
+    if (j.ctx->shape.precision != pool->precision || j.ctx->device != pool->device) return PEPS_EINVAL;
+    if (j.ctx->plan.slot_elems > pool->slot_elems || j.ctx->plan.slot_doubles > pool->slot_doubles)
+      return PEPS_EINVAL;
+    if (j.B > 0 && (!j.spins || !j.e_loc)) return PEPS_EINVAL;
+  }
+  if (cudaSetDevice(pool->device) != cudaSuccess) return PEPS_ECUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return pool->precision == PEPS_FP64 ? launch_multi<double>(pool, jobs, n_jobs, st)
+                                      : launch_multi<ff>(pool, jobs, n_jobs, st);
+}
+
+int peps_pool_sync_status(peps_pool* p, void* stream, int32_t* flags) {
+  if (!p) return PEPS_EINVAL;
+  if (cudaSetDevice(p->device) != cudaSuccess) return PEPS_ECUDA;
+  if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return PEPS_ECUDA;
+  int h = 0;
+  if (cudaMemcpy(&h, p->flags, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemset(p->flags, 0, sizeof(int)) != cudaSuccess)
+    return PEPS_ECUDA;
+  if (flags) *flags = h;
+  return h ? PEPS_ENUMERIC : PEPS_OK;
+}
+
 int peps_sync_status(peps_ctx* c, void* stream, int32_t* flags) {
   if (!c) return PEPS_EINVAL;
   if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, PEPS_ECUDA, "cudaSetDevice failed");

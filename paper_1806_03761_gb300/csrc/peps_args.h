@@ -57,3 +57,11 @@ struct CorrArgs {
   double* wsd;
   int* flags;
 };
+
+// One job of a multi-job launch (peps_multi_kernel): the job's evaluation
+// arguments and the number of its first (job, sample) item.
+template <class R>
+struct MultiJobDev {
+  EvalArgs<R> a;
+  int64_t first_item;
+};

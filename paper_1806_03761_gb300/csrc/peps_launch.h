@@ -8,6 +8,7 @@
 template <class R> struct EvalArgs;
 template <class R> struct SampleArgs;
 template <class R> struct CorrArgs;
+template <class R> struct MultiJobDev;
 
 cudaError_t peps_launch_eval_f64(const EvalArgs<double>& a, int grid, cudaStream_t st);
 cudaError_t peps_launch_eval_ff(const EvalArgs<ff>& a, int grid, cudaStream_t st);
@@ -32,3 +33,11 @@ cudaError_t peps_launch_corr_mean(const double* ss, int64_t B, int64_t len, doub
 cudaError_t peps_launch_structure_factor(const double* mean, int L, int N, const int32_t* pos,
                                          int nbulk, const int32_t* bulk, double kx, double ky,
                                          double* out, cudaStream_t st);
+cudaError_t peps_launch_multi_f64(const MultiJobDev<double>* jobs, int n_jobs, int64_t n_items,
+                                  unsigned long long* next, double* ws, double* wsd,
+                                  int64_t slot_elems, int64_t slot_doubles, int* flags, int grid,
+                                  cudaStream_t st);
+cudaError_t peps_launch_multi_ff(const MultiJobDev<ff>* jobs, int n_jobs, int64_t n_items,
+                                 unsigned long long* next, ff* ws, double* wsd,
+                                 int64_t slot_elems, int64_t slot_doubles, int* flags, int grid,
+                                 cudaStream_t st);

@@ -7,10 +7,11 @@
 //
 // Error-free splitting (Ozaki, Ogita, Oishi and Rump, Numer. Algorithms 59,
 // 2012).  Row i of A is scaled by 2^-e_i (e_i: the exponent of its largest
-// entry) and cut into s slices of 7 bits: slice t holds the signed digit
-// q_t in [-127, 127] of |x| 2^-e_i = sum_t |q_t| 2^-7(t+1) + (a remainder
-// below 2^-7s), read off the bits of x with integer operations only (exact
-// in BF16); column j of B likewise with f_j.  A product of slices t_a and t_b
+// entry) and cut into s slices of 7 bits: slice t holds the digit q_t of
+// x 2^-e_i = sum_t q_t 2^-7(t+1) + (a remainder of at most 2^-7s-1), digits
+// balanced and rounded to nearest (|q_0| <= 128, |q_t| <= 64 after), read
+// off the bits of x with integer operations only (exact in BF16); column j
+// of B likewise with f_j.  A product of slices t_a and t_b
 // is an integer multiple of 2^-7(t_a+t_b+2) of magnitude < 2^14, so the K
 // products of every pair with the same g = t_a + t_b (at most s pairs) add up
 // exactly in an FP32 accumulator while K s <= 1024.  One TMEM accumulator per
@@ -105,10 +106,16 @@ __global__ void tc_split_kernel(const double* X, int64_t sb, int64_t rs, int64_t
       if (ex != 0) mag = sh >= 0 ? (mant << sh) : (-sh < 64 ? (mant >> -sh) : 0ull);
       const bool neg = (bits >> 63) != 0;
       const int64_t off = (k / TC_KC) * blk + tc_core_off(rr, k % TC_KC) / 2;
+      // balanced base-128 digits, each rounded to nearest (half up): digit
+      // t = round(rem / 2^(55-7t)), rem -= digit 2^(55-7t); the first lies in
+      // [0, 128], the others in [-64, 64], so the digits of different rows
+      // and columns carry both signs and the omitted high-order slice
+      // products cancel on average; |remainder| <= 2^-7s-1 of the scale
+      long long rem = (long long)mag;
       for (int t = 0; t < s; ++t) {
-        // digit t: bits 61-7t .. 55-7t, i.e. |x| 2^-e = sum_t d_t 2^-7(t+1)
-        // + (below 2^-7s), d_t in [0, 127], exact in BF16
-        const int d = (int)((mag >> (55 - TC_SLICE_BITS * t)) & 0x7F);
+        const int sh = 55 - TC_SLICE_BITS * t;
+        const long long d = (rem + (1ll << (sh - 1))) >> sh;  // arithmetic shift
+        rem -= d * (1ll << sh);
         base[(int64_t)t * nch * blk + off] = __float2bfloat16_rn((float)(neg ? -d : d));
       }
     }

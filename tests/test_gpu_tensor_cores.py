@@ -22,13 +22,13 @@ def _built():
 
 def first_slices(X, axis):
     """The one-slice image of X along `axis` (the reduction index): scale by
-    2^-e (e: exponent of the largest |entry| of each row or column) and keep
-    the first 7 bits (truncated toward zero); returns the slice values times
-    their scale."""
+    2^-e (e: exponent of the largest |entry| of each row or column) and round
+    to 7 bits (to nearest, halves away from zero); returns the slice values
+    times their scale."""
     mx = np.max(np.abs(X), axis=axis, keepdims=True)
     e = np.where(mx > 0, np.frexp(mx)[1], 0)
     r = np.ldexp(X, -e)
-    q = np.trunc(r * 128.0)
+    q = np.sign(r) * np.floor(np.abs(r) * 128.0 + 0.5)
     return np.ldexp(q / 128.0, e)
 
 
