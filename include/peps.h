@@ -327,6 +327,28 @@ int peps_local_energy_multi(peps_pool* pool, const peps_multi_job* jobs, int32_t
                             void* stream);
 int peps_pool_sync_status(peps_pool* pool, void* stream, int32_t* flags);
 
+/* The fused VMC step and the GO update with their Philox counters in device
+ * memory, for capture in a CUDA graph: counters is uint32[2] (device) with
+ * counters[0] the sweep number (as `sweep` of peps_vmc_step) and counters[1]
+ * the GO step number (as `step` of peps_grad_step), read by the kernels when
+ * they run; peps_counters_advance adds `inc` to counters[0 .. n-1] in a
+ * one-thread kernel.  A graph holding peps_vmc_step_dc, peps_grad_step_dc and
+ * peps_counters_advance(counters, 2, 1) therefore replays as successive VMC
+ * steps (Fig. "contraction", Steps 1-6 and the GO update), with results
+ * identical to the same steps called directly.  Arguments and errors
+ * otherwise as peps_vmc_step / peps_grad_step. */
+int peps_vmc_step_dc(peps_ctx* ctx, uint64_t seed, int64_t n_chains,
+                     int64_t chain_offset, const uint32_t* counters,
+                     uint8_t* chain_state, double* e_loc, double* log_abs,
+                     int8_t* sign, double* sum_delta, double* sum_delta_e,
+                     double* sum_e, int32_t accumulate, int64_t* accepted,
+                     void* stream);
+int peps_grad_step_dc(peps_ctx* ctx, const double* sum_delta,
+                      const double* sum_delta_e, const double* sum_e, int64_t M,
+                      double dt, uint64_t seed, const uint32_t* counters,
+                      double* A_inout, void* stream);
+int peps_counters_advance(uint32_t* counters, int32_t n, uint32_t inc, void* stream);
+
 /* Wait for `stream` and return the device-side error state: PEPS_OK, or
  * PEPS_ENUMERIC with *flags (host, nullable) set to the PEPS_FLAG_* bits
  * seen since the last call (the bits are cleared). */

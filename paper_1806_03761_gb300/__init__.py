@@ -230,6 +230,39 @@ class PepsContext:
                                                    self._stream()))
         return out
 
+    # -- device-resident counters (CUDA-graph capture) -------------------------
+    def new_counters(self, sweep, step):
+        """uint32[2] device counters: the next sweep number and GO step number."""
+        return self.torch.tensor([sweep, step], dtype=self.torch.int32, device=self.device)
+
+    def vmc_step_dc(self, seed, state, counters, chain_offset=0, sums=None, out=None):
+        """peps_vmc_step with the sweep number read from counters[0] at run time."""
+        t = self.torch
+        n = state.shape[0]
+        sums = sums or self.new_sums()
+        if out is None:
+            out = dict(e_loc=self._empty(n), log_abs=self._empty(n), sign=self._empty(n, dtype=t.int8))
+        self._check(self.lib.peps_vmc_step_dc(
+            self.h, int(seed), n, int(chain_offset), _ptr(counters), _ptr(state), _ptr(out["e_loc"]),
+            _ptr(out["log_abs"]), _ptr(out["sign"]), _ptr(sums[0]), _ptr(sums[1]), _ptr(sums[2]), 0,
+            None, self._stream()))
+        res = dict(out)
+        res.update(sum_delta=sums[0], sum_delta_e=sums[1], sum_e=sums[2])
+        return res
+
+    def grad_step_dc(self, sums, M, dt, seed, counters, A):
+        """peps_grad_step with the GO step number read from counters[1]."""
+        self._check(self.lib.peps_grad_step_dc(self.h, _ptr(sums[0]), _ptr(sums[1]), _ptr(sums[2]),
+                                               int(M), float(dt), int(seed), _ptr(counters), _ptr(A),
+                                               self._stream()))
+        return A
+
+    def advance_counters(self, counters, inc=1):
+        rc = self.lib.peps_counters_advance(_ptr(counters), int(counters.numel()), int(inc),
+                                            self._stream())
+        if rc != 0:
+            raise PepsError(rc, "peps_counters_advance failed")
+
     def sync_status(self):
         f = ctypes.c_int32(0)
         rc = self.lib.peps_sync_status(self.h, self._stream(), ctypes.byref(f))

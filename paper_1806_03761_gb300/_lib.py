@@ -30,7 +30,8 @@ EXPORTS = ("peps_create", "peps_destroy", "peps_last_error", "peps_workspace_byt
            "peps_server_create", "peps_server_submit", "peps_server_wait", "peps_server_destroy",
            "peps_correlations", "peps_structure_factor", "peps_tc_workspace_bytes", "peps_tc_gemm",
            "peps_cc_workspace_bytes", "peps_cc_gemm", "peps_pool_create", "peps_pool_destroy",
-           "peps_pool_slots", "peps_local_energy_multi", "peps_pool_sync_status")
+           "peps_pool_slots", "peps_local_energy_multi", "peps_pool_sync_status",
+           "peps_vmc_step_dc", "peps_grad_step_dc", "peps_counters_advance")
 
 
 class PepsShape(ctypes.Structure):
@@ -99,6 +100,9 @@ _SIGS = {
     "peps_pool_slots": (I32, [P, ctypes.POINTER(I32)]),
     "peps_local_energy_multi": (I32, [P, ctypes.POINTER(PepsMultiJob), I32, P]),
     "peps_pool_sync_status": (I32, [P, P, ctypes.POINTER(I32)]),
+    "peps_vmc_step_dc": (I32, [P, U64, I64, I64, P, P, P, P, P, P, P, P, I32, P, P]),
+    "peps_grad_step_dc": (I32, [P, P, P, P, I64, F64, U64, P, P, P]),
+    "peps_counters_advance": (I32, [P, I32, ctypes.c_uint32, P]),
 }
 
 

@@ -187,8 +187,9 @@ int launch_sample(peps_ctx* c, uint64_t seed, int64_t n_chains, int64_t chain_of
 
 template <class R>
 int launch_vmc(peps_ctx* c, uint64_t seed, int64_t n, int64_t chain_offset, uint64_t sweep,
-               uint8_t* state, double* e_loc, double* log_abs, int8_t* sign, double* sd,
-               double* sde, double* se, int accumulate, int64_t* accepted, cudaStream_t st) {
+               const uint32_t* sweep_dev, uint8_t* state, double* e_loc, double* log_abs,
+               int8_t* sign, double* sd, double* sde, double* se, int accumulate,
+               int64_t* accepted, cudaStream_t st) {
   EvalArgs<R> a;
   std::memset(&a, 0, sizeof(a));
   a.P = c->plan;
@@ -211,6 +212,7 @@ int launch_vmc(peps_ctx* c, uint64_t seed, int64_t n, int64_t chain_offset, uint
   s.n_chains = n;
   s.chain_offset = chain_offset;
   s.first_sweep = sweep;
+  s.sweep_dev = sweep_dev;
   s.state = state;
   s.accepted = accepted;
   int grid = (int)std::min<int64_t>(c->nslots, n);
@@ -385,7 +387,7 @@ int peps_grad_step(peps_ctx* c, const double* sum_delta, const double* sum_delta
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
   cudaError_t e = peps_launch_grad(c->shape.precision, sum_delta, sum_delta_e, sum_e, (double)M, dt,
-                                   k0, k1, (uint32_t)step, A_inout, c->As, n, st);
+                                   k0, k1, (uint32_t)step, nullptr, A_inout, c->As, n, st);
   if (e != cudaSuccess) return cuda_fail(c, e, "peps_grad_kernel launch");
   c->tensors_set = 1;
   return PEPS_OK;
@@ -418,10 +420,13 @@ int peps_sample_batch(peps_ctx* c, uint64_t seed, int64_t n_chains, int64_t chai
                            first_sweep, spins_out, chain_state, accepted, st);
 }
 
-int peps_vmc_step(peps_ctx* c, uint64_t seed, int64_t n_chains, int64_t chain_offset,
-                  uint64_t sweep, uint8_t* chain_state, double* e_loc, double* log_abs,
-                  int8_t* sign, double* sum_delta, double* sum_delta_e, double* sum_e,
-                  int32_t accumulate, int64_t* accepted, void* stream) {
+}  // extern "C"
+
+namespace {
+int vmc_common(peps_ctx* c, uint64_t seed, int64_t n_chains, int64_t chain_offset,
+               uint64_t sweep, const uint32_t* sweep_dev, uint8_t* chain_state, double* e_loc,
+               double* log_abs, int8_t* sign, double* sum_delta, double* sum_delta_e,
+               double* sum_e, int32_t accumulate, int64_t* accepted, void* stream) {
   if (!c) return PEPS_EINVAL;
   if (n_chains < 0) return fail(c, PEPS_EINVAL, "n_chains must be >= 0");
   if (chain_offset < 0 || chain_offset + n_chains > (int64_t(1) << 32))
@@ -436,13 +441,58 @@ int peps_vmc_step(peps_ctx* c, uint64_t seed, int64_t n_chains, int64_t chain_of
   if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, PEPS_ECUDA, "cudaSetDevice failed");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (c->shape.precision == PEPS_FP64)
-    return launch_vmc<double>(c, seed, n_chains, chain_offset, sweep, chain_state, e_loc, log_abs, sign,
-                              sum_delta, sum_delta_e, sum_e, accumulate, accepted, st);
+    return launch_vmc<double>(c, seed, n_chains, chain_offset, sweep, sweep_dev, chain_state, e_loc,
+                              log_abs, sign, sum_delta, sum_delta_e, sum_e, accumulate, accepted, st);
   if (c->shape.precision == PEPS_FP32)
-    return launch_vmc<float>(c, seed, n_chains, chain_offset, sweep, chain_state, e_loc, log_abs, sign,
-                             sum_delta, sum_delta_e, sum_e, accumulate, accepted, st);
-  return launch_vmc<ff>(c, seed, n_chains, chain_offset, sweep, chain_state, e_loc, log_abs, sign,
-                        sum_delta, sum_delta_e, sum_e, accumulate, accepted, st);
+    return launch_vmc<float>(c, seed, n_chains, chain_offset, sweep, sweep_dev, chain_state, e_loc,
+                             log_abs, sign, sum_delta, sum_delta_e, sum_e, accumulate, accepted, st);
+  return launch_vmc<ff>(c, seed, n_chains, chain_offset, sweep, sweep_dev, chain_state, e_loc,
+                        log_abs, sign, sum_delta, sum_delta_e, sum_e, accumulate, accepted, st);
+}
+}  // namespace
+
+extern "C" {
+
+int peps_vmc_step(peps_ctx* c, uint64_t seed, int64_t n_chains, int64_t chain_offset,
+                  uint64_t sweep, uint8_t* chain_state, double* e_loc, double* log_abs,
+                  int8_t* sign, double* sum_delta, double* sum_delta_e, double* sum_e,
+                  int32_t accumulate, int64_t* accepted, void* stream) {
+  return vmc_common(c, seed, n_chains, chain_offset, sweep, nullptr, chain_state, e_loc, log_abs,
+                    sign, sum_delta, sum_delta_e, sum_e, accumulate, accepted, stream);
+}
+
+int peps_vmc_step_dc(peps_ctx* c, uint64_t seed, int64_t n_chains, int64_t chain_offset,
+                     const uint32_t* counters, uint8_t* chain_state, double* e_loc,
+                     double* log_abs, int8_t* sign, double* sum_delta, double* sum_delta_e,
+                     double* sum_e, int32_t accumulate, int64_t* accepted, void* stream) {
+  if (c && !counters) return fail(c, PEPS_EINVAL, "counters is NULL");
+  return vmc_common(c, seed, n_chains, chain_offset, 0, counters, chain_state, e_loc, log_abs,
+                    sign, sum_delta, sum_delta_e, sum_e, accumulate, accepted, stream);
+}
+
+int peps_grad_step_dc(peps_ctx* c, const double* sum_delta, const double* sum_delta_e,
+                      const double* sum_e, int64_t M, double dt, uint64_t seed,
+                      const uint32_t* counters, double* A_inout, void* stream) {
+  if (!c) return PEPS_EINVAL;
+  if (!sum_delta || !sum_delta_e || !sum_e || !A_inout || !counters)
+    return fail(c, PEPS_EINVAL, "NULL argument");
+  if (M <= 0) return fail(c, PEPS_EINVAL, "M must be positive");
+  if (!std::isfinite(dt)) return fail(c, PEPS_EINVAL, "dt must be finite");
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, PEPS_ECUDA, "cudaSetDevice failed");
+  int64_t n = (int64_t)c->plan.N * 2 * c->plan.D4;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = peps_launch_grad(c->shape.precision, sum_delta, sum_delta_e, sum_e, (double)M, dt,
+                                   (uint32_t)seed, (uint32_t)(seed >> 32), 0, counters + 1, A_inout,
+                                   c->As, n, st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "peps_grad_kernel launch");
+  c->tensors_set = 1;
+  return PEPS_OK;
+}
+
+int peps_counters_advance(uint32_t* counters, int32_t n, uint32_t inc, void* stream) {
+  if (!counters || n < 1 || n > 64) return PEPS_EINVAL;
+  return peps_launch_counters(counters, n, inc, static_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? PEPS_OK : PEPS_ECUDA;
 }
 
 int peps_correlations(peps_ctx* c, const uint8_t* spins, int64_t B, int32_t n_src,

@@ -34,6 +34,7 @@ struct SampleArgs {
   int64_t n_chains, chain_offset;
   int n_burn, n_thin, spc;
   uint64_t first_sweep;
+  const uint32_t* sweep_dev;  // nullable: the fused step's sweep number, read at run time
   uint8_t* out;              // [n_chains*spc][N]
   uint8_t* state;            // [n_chains][N] or null (in/out)
   int64_t* accepted;         // [n_chains] or null

@@ -420,11 +420,14 @@ __global__ void peps_convert_kernel(const double* A, R* As, int64_t n, int* flag
   }
 }
 
-// GO update: A[e] -= p_e dt sign(g_e), g = 2 sde/M - 2 (sd/M)(se/M)
+// GO update: A[e] -= p_e dt sign(g_e), g = 2 sde/M - 2 (sd/M)(se/M); the step
+// number from step_dev when given (read at run time: graph replay)
 template <class R>
 __global__ void peps_grad_kernel(const double* sd, const double* sde, const double* se,
                                  double M, double dt, uint32_t k0, uint32_t k1,
-                                 uint32_t step, double* A, R* As, int64_t n) {
+                                 uint32_t step_in, const uint32_t* step_dev, double* A, R* As,
+                                 int64_t n) {
+  const uint32_t step = step_dev ? *step_dev : step_in;
   const double mE = se[0] / M;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
     double g = 2.0 * (sde[e] / M) - 2.0 * (sd[e] / M) * mE;

@@ -37,16 +37,17 @@ cudaError_t peps_launch_convert(int precision, const double* A, void* As, int64_
 
 cudaError_t peps_launch_grad(int precision, const double* sd, const double* sde, const double* se,
                              double M, double dt, uint32_t k0, uint32_t k1, uint32_t step,
-                             double* A, void* As, int64_t n, cudaStream_t st) {
+                             const uint32_t* step_dev, double* A, void* As, int64_t n,
+                             cudaStream_t st) {
   int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
   if (precision == PEPS_FP64)
-    peps_grad_kernel<double><<<grid, 256, 0, st>>>(sd, sde, se, M, dt, k0, k1, step, A,
+    peps_grad_kernel<double><<<grid, 256, 0, st>>>(sd, sde, se, M, dt, k0, k1, step, step_dev, A,
                                                    static_cast<double*>(As), n);
   else if (precision == PEPS_FP32)
-    peps_grad_kernel<float><<<grid, 256, 0, st>>>(sd, sde, se, M, dt, k0, k1, step, A,
+    peps_grad_kernel<float><<<grid, 256, 0, st>>>(sd, sde, se, M, dt, k0, k1, step, step_dev, A,
                                                   static_cast<float*>(As), n);
   else
-    peps_grad_kernel<ff><<<grid, 256, 0, st>>>(sd, sde, se, M, dt, k0, k1, step, A,
+    peps_grad_kernel<ff><<<grid, 256, 0, st>>>(sd, sde, se, M, dt, k0, k1, step, step_dev, A,
                                                static_cast<ff*>(As), n);
   return cudaGetLastError();
 }
@@ -93,5 +94,17 @@ cudaError_t peps_launch_structure_factor(const double* mean, int L, int N, const
                                          int nbulk, const int32_t* bulk, double kx, double ky,
                                          double* out, cudaStream_t st) {
   peps_structure_factor_kernel<<<1, 256, 0, st>>>(mean, L, N, pos, nbulk, bulk, kx, ky, out);
+  return cudaGetLastError();
+}
+
+// counters[i] += inc (one thread): advances the device-resident sweep and
+// step numbers between replays of a captured VMC step
+__global__ void peps_counters_add(uint32_t* c, int n, uint32_t inc) {
+  if (threadIdx.x == 0 && blockIdx.x == 0)
+    for (int i = 0; i < n; ++i) c[i] += inc;
+}
+
+cudaError_t peps_launch_counters(uint32_t* c, int n, uint32_t inc, cudaStream_t st) {
+  peps_counters_add<<<1, 32, 0, st>>>(c, n, inc);
   return cudaGetLastError();
 }

@@ -25,7 +25,9 @@ cudaError_t peps_launch_convert(int precision, const double* A, void* As, int64_
                                 cudaStream_t st);
 cudaError_t peps_launch_grad(int precision, const double* sd, const double* sde, const double* se,
                              double M, double dt, uint32_t k0, uint32_t k1, uint32_t step,
-                             double* A, void* As, int64_t n, cudaStream_t st);
+                             const uint32_t* step_dev, double* A, void* As, int64_t n,
+                             cudaStream_t st);
+cudaError_t peps_launch_counters(uint32_t* c, int n, uint32_t inc, cudaStream_t st);
 cudaError_t peps_launch_corr_f64(const CorrArgs<double>& a, int grid, cudaStream_t st);
 cudaError_t peps_launch_corr_ff(const CorrArgs<ff>& a, int grid, cudaStream_t st);
 cudaError_t peps_launch_corr_mean(const double* ss, int64_t B, int64_t len, double* mean,

@@ -227,7 +227,8 @@ __global__ void __launch_bounds__(PEPS_NT, PEPS_MINB) peps_vmc_kernel(EvalArgs<R
     const uint32_t chain = (uint32_t)(s.chain_offset + c);
     load_chain<R>(sh, s.state, c, N, chain, s.k0, s.k1);
     evaluate_one<R>(a, c, sh, w, ps, false);
-    const int acc = sweep_one<R>(P, a.steps, a.As, s.k0, s.k1, chain, (uint32_t)s.first_sweep,
+    const uint32_t sw = s.sweep_dev ? *s.sweep_dev : (uint32_t)s.first_sweep;
+    const int acc = sweep_one<R>(P, a.steps, a.As, s.k0, s.k1, chain, sw,
                                  sh, w, true);
     for (int m = threadIdx.x; m < N; m += blockDim.x) s.state[c * N + m] = sh.sp[m];
     if (threadIdx.x == 0 && s.accepted) s.accepted[c] = acc;
