@@ -51,6 +51,27 @@ def _ptr(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
 
 
+def _lib_for(L, D, Dc, precision):
+    """The library a context of this shape uses: the tuned variant named by
+    tuning.json for (L, D, Dc, form) when it has been built, else the
+    default build (always the default under PEPS_LIB)."""
+    import json
+    import os
+    from . import build as B
+    if os.environ.get("PEPS_LIB") or not os.path.exists(B.TUNING):
+        return _lib.load()
+    entry = json.load(open(B.TUNING)).get(tuning_key(L, D, Dc, precision))
+    if entry:
+        path = B.variant_path(entry["choice"], precision)
+        if path != B.LIB and os.path.exists(path):
+            return _lib.load_path(path)
+    return _lib.load()
+
+
+def tuning_key(L, D, Dc, precision):
+    return "%dx%d_D%d_Dc%d_%s" % (L, L, D, Dc, precision)
+
+
 class PepsContext:
     """One library context: shape, precision form and device workspace."""
 
@@ -59,7 +80,7 @@ class PepsContext:
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required (there is no CPU path)")
         self.torch = torch
-        self.lib = _lib.load()
+        self.lib = _lib_for(int(L), int(D), int(Dc), precision)
         self.L, self.D, self.Dc = int(L), int(D), int(Dc)
         self.N = self.L * self.L
         self.D4 = self.D ** 4

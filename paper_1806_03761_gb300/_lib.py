@@ -106,12 +106,32 @@ _SIGS = {
 }
 
 
+_variants = {}
+
+
+def load_path(path):
+    """Load a library built at `path` (a tuned variant) once and declare its
+    signatures."""
+    if path not in _variants:
+        if not os.path.exists(path):
+            raise RuntimeError("library variant not built: %s" % path)
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _variants[path] = lib
+    return _variants[path]
+
+
 def load(path=None):
-    """Load libpeps.so (once) and declare its signatures."""
+    """Load libpeps.so (once) and declare its signatures.  The environment
+    variable PEPS_LIB names another build of the library to load instead
+    (the autotuner's timing runs use it)."""
     global _lib
     if _lib is not None:
         return _lib
-    path = path or LIB_PATH
+    path = path or os.environ.get("PEPS_LIB") or LIB_PATH
     if not os.path.exists(path):
         raise RuntimeError(
             "libpeps.so not found at %s: build it with "

@@ -4,6 +4,14 @@ Every translation unit in csrc/ is compiled in parallel and the objects are
 linked into paper_1806_03761_gb300/lib/libpeps.so.  A unit is rebuilt when
 it or any header in csrc/ or include/ is newer than its object.
 
+Tuned variants (paper_1806_03761_gb300/tuning.json, written by the
+autotuner): a variant sets compile-time knobs of the kernels (PEPS_QR_NB,
+PEPS_BA_FF, PEPS_BA_F64, PEPS_MINB, PEPS_NT).  It recompiles the units those
+knobs reach for one precision form -- the C ABI and the form's fused
+VMC-step kernel -- and links them with the default objects of every other
+unit (device code is compiled per unit, without relocatable device code, so
+the units share no device functions) into lib/<tag>/libpeps.so.
+
     python -m paper_1806_03761_gb300.build [--verbose]
 """
 import concurrent.futures as cf
@@ -38,15 +46,85 @@ def _headers_mtime():
     return max(os.path.getmtime(h) for h in hs)
 
 
-def _compile(src, obj, verbose):
-    cmd = [nvcc()] + ARCH + FLAGS + (["-Xptxas", "-v"] if verbose else []) + ["-c", src, "-o", obj]
+def _compile(src, obj, verbose, extra=()):
+    cmd = [nvcc()] + ARCH + FLAGS + list(extra) + (["-Xptxas", "-v"] if verbose else []) + \
+        ["-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("nvcc failed on %s:\n%s%s" % (src, r.stdout, r.stderr))
     return (src, r.stderr if verbose else "")
 
 
+DEFAULTS = {"PEPS_QR_NB": 4, "PEPS_BA_FF": 4, "PEPS_BA_F64": 2, "PEPS_MINB": 2, "PEPS_NT": 256}
+FORMS = {"fp64": "f64", "mixed": "ff", "fp32": "f32"}
+TUNING = os.path.join(PKG, "tuning.json")
+
+
+def variant_tag(knobs, precision):
+    """Directory name of a variant: the form and every knob that differs from
+    the default, e.g. 'mixed-PEPS_QR_NB8'; 'default' when none differs."""
+    diff = sorted((k, v) for k, v in knobs.items() if DEFAULTS.get(k) != v)
+    if not diff:
+        return "default"
+    return precision + "-" + "-".join("%s%d" % (k, v) for k, v in diff)
+
+
+def variant_path(knobs, precision):
+    tag = variant_tag(knobs, precision)
+    return LIB if tag == "default" else os.path.join(LIBDIR, tag, "libpeps.so")
+
+
+def build_variant(knobs, precision, verbose=False):
+    """Build the library of one tuned variant (the default objects must exist:
+    call build() first); returns its path."""
+    tag = variant_tag(knobs, precision)
+    if tag == "default":
+        return LIB
+    out_dir = os.path.join(BUILD, tag)
+    lib_dir = os.path.join(LIBDIR, tag)
+    os.makedirs(out_dir, exist_ok=True)
+    os.makedirs(lib_dir, exist_ok=True)
+    flags = ["-D%s=%d" % (k, v) for k, v in sorted(knobs.items())]
+    units = ["peps_api.cu", "peps_k_vmc_%s.cu" % FORMS[precision]]
+    hmt = _headers_mtime()
+    jobs = []
+    for u in units:
+        src = os.path.join(CSRC, u)
+        obj = os.path.join(out_dir, u[:-3] + ".o")
+        if not os.path.exists(obj) or os.path.getmtime(obj) < max(hmt, os.path.getmtime(src)):
+            jobs.append((src, obj))
+    with cf.ThreadPoolExecutor(max_workers=max(1, len(jobs))) as ex:
+        list(ex.map(lambda j: _compile(j[0], j[1], verbose, flags), jobs))
+    objs = [os.path.join(out_dir, u[:-3] + ".o") for u in units]
+    for o in sorted(glob.glob(os.path.join(BUILD, "*.o"))):
+        if os.path.basename(o)[:-2] + ".cu" not in units:
+            objs.append(o)
+    lib = os.path.join(lib_dir, "libpeps.so")
+    cmd = [nvcc()] + ARCH + ["-shared", "-o", lib] + objs + ["-lcudart"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
+    return lib
+
+
+def tuned_variants():
+    """[(knobs, precision)] of the tuning table's choices."""
+    import json
+    if not os.path.exists(TUNING):
+        return []
+    table = json.load(open(TUNING))
+    return [(dict(v["choice"]), v["precision"]) for v in table.values()]
+
+
 def build(verbose=False, force=False):
+    """Compile and link libpeps.so and the tuned variants; returns its path."""
+    lib = build_default(verbose, force)
+    for knobs, prec in tuned_variants():
+        build_variant(knobs, prec, verbose)
+    return lib
+
+
+def build_default(verbose=False, force=False):
     """Compile and link libpeps.so; returns its path."""
     os.makedirs(BUILD, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)

@@ -93,10 +93,17 @@ __device__ __forceinline__ Ctr ctr_init() {
 // is unchanged).  Otherwise each thread computes two
 // outputs adjacent in the fastest digit (shared loads where an operand does
 // not carry it).
-// Outputs per thread along the A-only digit: 4 for the FP32-word forms, 2 for
-// FP64 (whose accumulators take twice the registers; measured slower at 4).
-template <class R> struct ContractBlock { static constexpr int BA = 4; };
-template <> struct ContractBlock<double> { static constexpr int BA = 2; };
+// Outputs per thread along the A-only digit: PEPS_BA_FF (default 4) for the
+// FP32-word forms, PEPS_BA_F64 (default 2) for FP64, whose accumulators take
+// twice the registers (measured slower at 4); the autotuner varies them.
+#ifndef PEPS_BA_FF
+#define PEPS_BA_FF 4
+#endif
+#ifndef PEPS_BA_F64
+#define PEPS_BA_F64 2
+#endif
+template <class R> struct ContractBlock { static constexpr int BA = PEPS_BA_FF; };
+template <> struct ContractBlock<double> { static constexpr int BA = PEPS_BA_F64; };
 
 template <class R>
 __device__ void contract(const Ctr& d, const R* A, const R* B, R* C) {
