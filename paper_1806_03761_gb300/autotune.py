@@ -5,8 +5,10 @@ irregular contraction shapes, Sec. "Implementation on Sunway TaihuLight").
 Knobs: PEPS_QR_NB (Householder panel width; it also sets the panel capacity
 of the blocked bidiagonalisation), PEPS_BA_FF / PEPS_BA_F64 (outputs per
 thread along the A-only digit of a contraction), PEPS_MINB (blocks per SM
-the register budget is set for; the default slot count is this many per SM)
-and PEPS_NT (threads per block).  Search: the default, then one knob changed
+the register budget is set for; the default slot count is this many per SM),
+PEPS_NT (threads per block), and two code paths: PEPS_QR_PREFETCH (the next
+trailing column of the blocked QR prefetched into L1) and PEPS_BIDIAG_TPC
+(A'^T v of the bidiagonalisation with one thread per column).  Search: the default, then one knob changed
 at a time (a coordinate step); every candidate library is built (the C ABI
 and the form's fused kernel recompiled, see build.py), then timed in its own
 process on one wave of chains of the shape: one warm-up VMC step and --steps
@@ -27,6 +29,9 @@ from . import build as B
 
 CANDIDATES = [
     {},                                   # the default
+    {"PEPS_QR_PREFETCH": 1},
+    {"PEPS_BIDIAG_TPC": 1},
+    {"PEPS_QR_PREFETCH": 1, "PEPS_BIDIAG_TPC": 1},
     {"PEPS_QR_NB": 8},
     {"PEPS_QR_NB": 2},
     {"PEPS_BA_FF": 2, "PEPS_BA_F64": 1},

@@ -322,6 +322,15 @@ __device__ void householder_r_unblocked(R* X, int m, int n, R* Rout, R* sh) {
 #ifndef PEPS_QR_NB
 #define PEPS_QR_NB 4
 #endif
+// Autotuned code paths (0 / 1): prefetch a warp's next trailing column of the
+// blocked QR into L1; form A'^T v of the bidiagonalisation with one thread
+// per column instead of one warp per column.
+#ifndef PEPS_QR_PREFETCH
+#define PEPS_QR_PREFETCH 0
+#endif
+#ifndef PEPS_BIDIAG_TPC
+#define PEPS_BIDIAG_TPC 0
+#endif
 #define PEPS_QR_ROWS 896
 
 // Apply the panel's reflectors (explicit vectors v_s, zero above row s and
@@ -345,6 +354,14 @@ __device__ __forceinline__ void qr_trailing(R* X, int m, int n, int k0, int mr, 
       const int i = lane + q * PEPS_WARP;
       xr[q] = i < mr ? x[i] : M::zero();
     }
+#if PEPS_QR_PREFETCH
+    // the warp's next column into L1 while this one is updated
+    if (c + nw < n) {
+      const R* xn = x + (int64_t)nw * m;
+      for (int i = lane * (128 / (int)sizeof(R)); i < mr; i += PEPS_WARP * (128 / (int)sizeof(R)))
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(xn + i));
+    }
+#endif
     // w = V^T x
     typename M::acc_t a[PEPS_QR_NB];
 #pragma unroll
@@ -744,6 +761,26 @@ __device__ void bidiag_blocked(R* A, int m, int p, int nb, R* d, R* e, R* tau, R
       // (c) Y[:, j] = tau_q (A'^T v) over columns k+1..p-1, with
       //     A'^T v = A^T v - Y (V^T v) - U (W^T v)
       if (M::hi(tq) != 0) {
+#if PEPS_BIDIAG_TPC
+        // one thread per column: a sequential dot product (two accumulators),
+        // v read from shared memory by all threads at once
+        for (int q = t; q < nc + 2 * j; q += nt) {
+          const int l = q - nc;  // l < j: V^T v, else W^T v
+          const R* col = q < nc ? A + (int64_t)(k + 1 + q) * m : (l < j ? Vp + l * m : Wp + (l - j) * m);
+          typename M::acc_t a0, a1;
+          M::acc_init(a0);
+          M::acc_init(a1);
+          int i = k;
+          for (; i + 1 < m; i += 2) {
+            M::mac(a0, col[i], v[i]);
+            M::mac(a1, col[i + 1], v[i + 1]);
+          }
+          if (i < m) M::mac(a0, col[i], v[i]);
+          const R r = M::acc_get(a0) + M::acc_get(a1);
+          if (q < nc) Yp[j * p + k + 1 + q] = r;
+          else cf[q - nc] = r;
+        }
+#else
         for (int q = wid; q < nc + 2 * j; q += nw) {
           typename M::acc_t a;
           M::acc_init(a);
@@ -761,6 +798,7 @@ __device__ void bidiag_blocked(R* A, int m, int p, int nb, R* d, R* e, R* tau, R
             else cf[q - nc] = r;
           }
         }
+#endif
       }
       __syncthreads();
       for (int c = t; c < p; c += nt) {
