@@ -45,9 +45,9 @@ FP64_MAX_WARMUP, FP64_MAX_STEPS = 2, 5
 # profiles/ give the command).  Keyed by (workload, precision form); only
 # valid for the kernel the capture was taken from.
 TRAFFIC_PER_CHAIN = {
-    # 32-chain launch: 8.236 GB read + 44.288 GB written
+    # 32-chain launch: 8.236 GB read + 44.986 GB written
     # (profiles/peps_vmc_16x16_D6_Dc24_mixed_traffic.md)
-    ("16x16_D6_Dc24", "mixed"): (8235671296 + 44288288000) / 32,
+    ("16x16_D6_Dc24", "mixed"): (8235538432 + 44985864448) / 32,
 }
 METRIC = "local-energy samples/s at 16x16 D=6 Dc=24, mixed vs FP64; p50/p99 latency"
 

@@ -116,7 +116,8 @@ __global__ void tc_split_kernel(const double* X, int64_t sb, int64_t rs, int64_t
         const int sh = 55 - TC_SLICE_BITS * t;
         const long long d = (rem + (1ll << (sh - 1))) >> sh;  // arithmetic shift
         rem -= d * (1ll << sh);
-        base[(int64_t)t * nch * blk + off] = __float2bfloat16_rn((float)(neg ? -d : d));
+        const int di = (int)d;  // |d| <= 128: a 32-bit conversion
+        base[(int64_t)t * nch * blk + off] = __int2bfloat16_rn(neg ? -di : di);
       }
     }
   }
