@@ -9,9 +9,10 @@ One step = one variational Monte Carlo iteration over a batch of B chains:
   2. the deterministic reduction of the per-slot sums,
   3. peps_grad_step: the sign update of the GO step.
 The metric is local-energy samples/s = B / device time of the step (chain
-states and tensors resident in HBM).  Every timed step also copies the chain
-states in from pinned host memory and the energies out, outside the device
-timing of `value` and inside that of `e2e`.
+states and tensors resident in HBM).  `e2e` is the same metric through the
+host-buffer entry point peps_vmc_step_host: every step copies the chain
+states in from pinned host memory and the advanced states, the energies and
+sum E out (up to E2E_MAX_STEPS steps after the timed ones).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
                     [--batch B] [--workload NAME] [--impl gb300|reference]
@@ -38,6 +39,7 @@ from synth import CONFIGS, make_peps  # noqa: E402
 
 WORKLOAD = "16x16_D6_Dc24"
 FP64_MAX_WARMUP, FP64_MAX_STEPS = 2, 5
+E2E_MAX_STEPS = 3
 
 # DRAM traffic of one launch of the fused kernel, bytes per chain (ncu
 # dram__bytes_read.sum + dram__bytes_write.sum over a smaller launch of the
@@ -435,42 +437,52 @@ def main():
     torch.cuda.synchronize()
     barrier(world)
 
-    # pinned host buffers of the end-to-end path
-    host_state = torch.empty(B, N, dtype=torch.uint8).pin_memory()
-    host_state.copy_(state)
-    host_e = torch.empty(B, dtype=torch.float64).pin_memory()
-    host_se = torch.empty(1, dtype=torch.float64).pin_memory()
-
     clocks = ClockSampler(local)
     clocks.start()
     torch.cuda.synchronize()
     barrier(world)
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
-    t_start, t_end = ev(), ev()
     marks = []
-    t_start.record(stream)
     for _ in range(args.steps):
-        k0, k1, k2, k3 = ev(), ev(), ev(), ev()
-        k0.record(stream)
-        state.copy_(host_state, non_blocking=True)        # H2D: chain states
+        k1, k2 = ev(), ev()
         k1.record(stream)
         vmc_step(ctx, state, sums, out, M_total)
         k2.record(stream)
-        host_e.copy_(out["e_loc"], non_blocking=True)     # D2H: energies, sum E
-        host_se.copy_(sums[2], non_blocking=True)
-        host_state.copy_(state, non_blocking=True)         # and the advanced chains
-        k3.record(stream)
-        stream.synchronize()
-        marks.append((k0, k1, k2, k3))
-    t_end.record(stream)
+        marks.append((k1, k2))
     torch.cuda.synchronize()
     barrier(world)
     clk = clocks.stop()
     rc, flags = ctx.sync_status()
-    step_ms = [a.elapsed_time(b) for _, a, b, _ in marks]
-    e2e_ms = [a.elapsed_time(b) for a, _, _, b in marks]
+    step_ms = [a.elapsed_time(b) for a, b in marks]
     dev_ms = max_over_ranks(float(np.sum(step_ms)), world) / max(args.steps, 1)
-    e2e_total = max_over_ranks(t_start.elapsed_time(t_end), world) / max(args.steps, 1)
+
+    # end to end through the host-buffer entry point: every step copies the
+    # chain states in from pinned host memory and the advanced states, the
+    # energies and sum E back (peps_vmc_step_host), then the GO update
+    e2e_steps = max(1, min(args.steps, E2E_MAX_STEPS))
+    host_state = torch.empty(B, N, dtype=torch.uint8).pin_memory()
+    host_state.copy_(state)
+    host_e = torch.empty(B, dtype=torch.float64).pin_memory()
+    host_se = torch.empty(1, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    barrier(world)
+    e2e_marks = []
+    for _ in range(e2e_steps):
+        k0, k3 = ev(), ev()
+        k0.record(stream)
+        ctx.vmc_step_host(seed, host_state, counters["sweep"], sums, host_e, host_se,
+                          chain_offset=chain_offset)
+        counters["sweep"] += 1
+        allreduce_sums(sums, world)
+        ctx.grad_step(sums, M_total, args.dt, seed, counters["step"], A)
+        counters["step"] += 1
+        k3.record(stream)
+        stream.synchronize()
+        e2e_marks.append((k0, k3))
+    e2e_ms = [a.elapsed_time(b) for a, b in e2e_marks]
+    e2e_total = max_over_ranks(float(np.sum(e2e_ms)), world) / e2e_steps
+    rc2, flags2 = ctx.sync_status()
+    rc, flags = rc or rc2, flags | flags2
 
     # the mixed form against the FP64 GPU path: the same batch of chains and
     # the same step, timed the same way (warm-up and timed steps capped at
@@ -568,9 +580,10 @@ def main():
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": M_total / (e2e_total / 1e3), "unit": "samples/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "ms_per_step": e2e_total, "copy_ms_per_step": float(np.mean(e2e_ms) - np.mean(step_ms))},
+                    "ms_per_step": e2e_total, "steps": e2e_steps,
+                    "call": "peps_vmc_step_host (pinned host buffers) + peps_grad_step"},
             "fp64_gpu": fp64,
-            "gpu_launches": 3 * args.steps, "clocks": clk,
+            "gpu_launches": 3 * (args.steps + e2e_steps), "clocks": clk,
             "status": {"rc": rc, "flags": flags}}
     print(json.dumps(line), flush=True)
 

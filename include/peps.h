@@ -327,6 +327,23 @@ int peps_local_energy_multi(peps_pool* pool, const peps_multi_job* jobs, int32_t
                             void* stream);
 int peps_pool_sync_status(peps_pool* pool, void* stream, int32_t* flags);
 
+/* peps_vmc_step from and to HOST memory, for callers that hold the chains on
+ * the host: chain_state (uint8[n_chains][N], host, in/out) is copied in, the
+ * fused step runs (Fig. "contraction", Steps 1-6), and the advanced states,
+ * e_loc (float64[n_chains], host), log_abs and sign (host, nullable) and
+ * sum_e (float64[1], host, nullable: the batch's sum of E(S)) are copied
+ * back; the call returns when they are there (stream synchronised).  The
+ * gradient sums stay on the device: sum_delta, sum_delta_e, sum_e_dev as in
+ * peps_vmc_step (all three NULL: the context's own, not returned).  Pinned
+ * host memory makes the copies asynchronous with respect to other streams.
+ * The context's device staging grows on the first call with a larger
+ * n_chains (an allocation). */
+int peps_vmc_step_host(peps_ctx* ctx, uint64_t seed, int64_t n_chains,
+                       int64_t chain_offset, uint64_t sweep, uint8_t* chain_state,
+                       double* e_loc, double* log_abs, int8_t* sign, double* sum_e,
+                       double* sum_delta, double* sum_delta_e, double* sum_e_dev,
+                       void* stream);
+
 /* The fused VMC step and the GO update with their Philox counters in device
  * memory, for capture in a CUDA graph: counters is uint32[2] (device) with
  * counters[0] the sweep number (as `sweep` of peps_vmc_step) and counters[1]

@@ -251,6 +251,18 @@ class PepsContext:
                                                    self._stream()))
         return out
 
+    def vmc_step_host(self, seed, state, sweep, sums, e_loc, sum_e=None, chain_offset=0):
+        """peps_vmc_step_host: `state` (uint8 [n, N]), `e_loc` (float64 [n]) and
+        `sum_e` (float64 [1], optional) are HOST tensors (pinned for
+        asynchronous copies); `sums` the device gradient sums.  Returns when
+        the results are in host memory."""
+        n = state.shape[0]
+        assert not state.is_cuda and not e_loc.is_cuda and state.is_contiguous()
+        self._check(self.lib.peps_vmc_step_host(
+            self.h, int(seed), n, int(chain_offset), int(sweep), _ptr(state), _ptr(e_loc), None, None,
+            _ptr(sum_e), _ptr(sums[0]), _ptr(sums[1]), _ptr(sums[2]), self._stream()))
+        return e_loc
+
     # -- device-resident counters (CUDA-graph capture) -------------------------
     def new_counters(self, sweep, step):
         """uint32[2] device counters: the next sweep number and GO step number."""

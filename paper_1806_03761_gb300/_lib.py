@@ -31,7 +31,7 @@ EXPORTS = ("peps_create", "peps_destroy", "peps_last_error", "peps_workspace_byt
            "peps_correlations", "peps_structure_factor", "peps_tc_workspace_bytes", "peps_tc_gemm",
            "peps_cc_workspace_bytes", "peps_cc_gemm", "peps_pool_create", "peps_pool_destroy",
            "peps_pool_slots", "peps_local_energy_multi", "peps_pool_sync_status",
-           "peps_vmc_step_dc", "peps_grad_step_dc", "peps_counters_advance")
+           "peps_vmc_step_dc", "peps_grad_step_dc", "peps_counters_advance", "peps_vmc_step_host")
 
 
 class PepsShape(ctypes.Structure):
@@ -103,6 +103,7 @@ _SIGS = {
     "peps_vmc_step_dc": (I32, [P, U64, I64, I64, P, P, P, P, P, P, P, P, I32, P, P]),
     "peps_grad_step_dc": (I32, [P, P, P, P, I64, F64, U64, P, P, P]),
     "peps_counters_advance": (I32, [P, I32, ctypes.c_uint32, P]),
+    "peps_vmc_step_host": (I32, [P, U64, I64, I64, U64, P, P, P, P, P, P, P, P, P]),
 }
 
 

@@ -24,6 +24,12 @@ struct peps_ctx {
   double* psum = nullptr;  // slot partial sums
   int* flags = nullptr;
   int32_t* idx = nullptr;  // 3N int32: correlation sources, bulk positions, bulk sites
+  // device staging of the host-buffer VMC step (grown on demand)
+  uint8_t* h_state = nullptr;
+  double* h_out = nullptr;  // e_loc [n], log_abs [n]
+  int8_t* h_sign = nullptr;
+  double* h_sums = nullptr; // sum_delta, sum_delta_e, sum_e
+  int64_t h_cap = 0;
   int nslots = 0;
   int tensors_set = 0;
   int device = 0;
@@ -325,6 +331,10 @@ int peps_destroy(peps_ctx* c) {
   cudaFree(c->psum);
   cudaFree(c->flags);
   cudaFree(c->idx);
+  cudaFree(c->h_state);
+  cudaFree(c->h_out);
+  cudaFree(c->h_sign);
+  cudaFree(c->h_sums);
   delete c;
   return PEPS_OK;
 }
@@ -459,6 +469,65 @@ int peps_vmc_step(peps_ctx* c, uint64_t seed, int64_t n_chains, int64_t chain_of
                   int32_t accumulate, int64_t* accepted, void* stream) {
   return vmc_common(c, seed, n_chains, chain_offset, sweep, nullptr, chain_state, e_loc, log_abs,
                     sign, sum_delta, sum_delta_e, sum_e, accumulate, accepted, stream);
+}
+
+int peps_vmc_step_host(peps_ctx* c, uint64_t seed, int64_t n_chains, int64_t chain_offset,
+                       uint64_t sweep, uint8_t* chain_state, double* e_loc, double* log_abs,
+                       int8_t* sign, double* sum_e, double* sum_delta, double* sum_delta_e,
+                       double* sum_e_dev, void* stream) {
+  if (!c) return PEPS_EINVAL;
+  if (n_chains < 1) return fail(c, PEPS_EINVAL, "n_chains must be >= 1");
+  if (!chain_state || !e_loc) return fail(c, PEPS_EINVAL, "chain_state and e_loc are required");
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, PEPS_ECUDA, "cudaSetDevice failed");
+  const int64_t N = c->plan.N;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (n_chains > c->h_cap) {  // staging grown (allocation: before any timed use)
+    cudaFree(c->h_state);
+    cudaFree(c->h_out);
+    cudaFree(c->h_sign);
+    c->h_state = nullptr; c->h_out = nullptr; c->h_sign = nullptr;
+    c->h_cap = 0;
+    if (cudaMalloc(&c->h_state, (size_t)n_chains * N) != cudaSuccess ||
+        cudaMalloc(&c->h_out, (size_t)n_chains * 2 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->h_sign, (size_t)n_chains) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, PEPS_ENOMEM, "staging of the host-buffer step");
+    }
+    c->h_cap = n_chains;
+  }
+  double* sd = sum_delta;
+  double* sde = sum_delta_e;
+  double* se = sum_e_dev;
+  if (!sd || !sde || !se) {  // the context's own sums
+    if (!c->h_sums &&
+        cudaMalloc(&c->h_sums, (2 * (size_t)N * 2 * c->plan.D4 + 1) * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, PEPS_ENOMEM, "gradient sums of the host-buffer step");
+    }
+    sd = c->h_sums;
+    sde = sd + (size_t)N * 2 * c->plan.D4;
+    se = sde + (size_t)N * 2 * c->plan.D4;
+  }
+  if (cudaMemcpyAsync(c->h_state, chain_state, (size_t)n_chains * N, cudaMemcpyHostToDevice, st) !=
+      cudaSuccess)
+    return fail(c, PEPS_ECUDA, "copying the chain states in");
+  int rc = vmc_common(c, seed, n_chains, chain_offset, sweep, nullptr, c->h_state, c->h_out,
+                      c->h_out + n_chains, c->h_sign, sd, sde, se, 0, nullptr, stream);
+  if (rc != PEPS_OK) return rc;
+  bool ok = cudaMemcpyAsync(chain_state, c->h_state, (size_t)n_chains * N, cudaMemcpyDeviceToHost, st) ==
+                cudaSuccess &&
+            cudaMemcpyAsync(e_loc, c->h_out, (size_t)n_chains * sizeof(double), cudaMemcpyDeviceToHost,
+                            st) == cudaSuccess;
+  if (ok && log_abs)
+    ok = cudaMemcpyAsync(log_abs, c->h_out + n_chains, (size_t)n_chains * sizeof(double),
+                         cudaMemcpyDeviceToHost, st) == cudaSuccess;
+  if (ok && sign)
+    ok = cudaMemcpyAsync(sign, c->h_sign, (size_t)n_chains, cudaMemcpyDeviceToHost, st) == cudaSuccess;
+  if (ok && sum_e)
+    ok = cudaMemcpyAsync(sum_e, se, sizeof(double), cudaMemcpyDeviceToHost, st) == cudaSuccess;
+  if (!ok) return fail(c, PEPS_ECUDA, "copying the results out");
+  if (cudaStreamSynchronize(st) != cudaSuccess) return fail(c, PEPS_ECUDA, "cudaStreamSynchronize");
+  return PEPS_OK;
 }
 
 int peps_vmc_step_dc(peps_ctx* c, uint64_t seed, int64_t n_chains, int64_t chain_offset,
