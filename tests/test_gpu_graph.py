@@ -67,3 +67,29 @@ def test_graph_replay_equals_direct_steps(prec):
     assert np.array_equal(d[2], gr[2])
     for a, b in zip(d[3], gr[3]):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_host_buffer_step_equals_device_step(prec):
+    """peps_vmc_step_host (chain states, energies and sum E in host memory)
+    gives the device step's states, energies and sums bit for bit."""
+    from paper_1806_03761_gb300 import PepsContext
+    L, D, Dc, n, seed = 5, 2, 4, 7, 1357
+    A = torch.from_numpy(make_peps(L, D, seed=34)).cuda()
+    ctx = PepsContext(L, D, Dc, precision=prec, slots=3)
+    ctx.set_tensors(A)
+    state = ctx.sample(seed, n, 2, 1, 1).contiguous()
+    host_state = state.cpu().pin_memory()
+    dev = ctx.vmc_step(seed, state, 7)
+    sums = ctx.new_sums()
+    host_e = torch.empty(n, dtype=torch.float64).pin_memory()
+    host_se = torch.empty(1, dtype=torch.float64).pin_memory()
+    ctx.vmc_step_host(seed, host_state, 7, sums, host_e, host_se)
+    torch.cuda.synchronize()
+    assert torch.equal(host_state, state.cpu())
+    assert torch.equal(host_e, dev["e_loc"].cpu())
+    assert torch.equal(host_se, dev["sum_e"].cpu())
+    for a, b in zip(sums, (dev["sum_delta"], dev["sum_delta_e"], dev["sum_e"])):
+        assert torch.equal(a, b)
+    assert ctx.sync_status()[0] == 0
+    ctx.close()
