@@ -67,7 +67,7 @@ def parse():
     p.add_argument("--slots", type=int, default=0)
     p.add_argument("--dt", type=float, default=1e-3)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--mode", default="vmc", choices=["vmc", "serving", "contraction"],
+    p.add_argument("--mode", default="vmc", choices=["vmc", "serving", "contraction", "correlations"],
                    help="serving: a Poisson stream of evaluation jobs through peps_server_*; "
                         "contraction: tensor-core vs CUDA-core column-step contractions")
     p.add_argument("--arrival-s", type=float, default=20.0,
@@ -381,10 +381,62 @@ def run_contraction(args):
     print(json.dumps(line), flush=True)
 
 
+def run_correlations(args):
+    """--mode correlations: <S_0 . S_m> for the centre source over one wave of
+    configurations of the workload (peps_correlations; items (sample, source)
+    one per block), and M^2 = m_s^2(pi, pi) over the bulk of an 8x8 lattice
+    with every bulk site a source; device time (CUDA events, mean of --steps
+    after --warmup)."""
+    import torch
+
+    import paper_1806_03761_gb300 as P
+    from synth import make_peps, random_sz0_configs
+    stream = torch.cuda.current_stream()
+    rows = []
+    for (wl, bulk_sources) in ((args.workload, False), ("8x8_D4_Dc16", True)):
+        cfg = dict(CONFIGS[wl])
+        L, D, Dc = cfg["L"], cfg["D"], cfg["Dc"]
+        A = torch.from_numpy(make_peps(L, D, cfg["seed"], cfg["recipe"], cfg.get("eps", 1e-2))).cuda()
+        ctx = P.PepsContext(L, D, Dc, precision=args.precision)
+        ctx.set_tensors(A)
+        if bulk_sources:
+            lo, hi = (2, L - 2) if L > 4 else (0, L)
+            sources = [i * L + j for i in range(lo, hi) for j in range(lo, hi)]
+            B = max(1, ctx.slots // len(sources))
+        else:
+            sources = [(L // 2) * L + L // 2]
+            B = ctx.slots
+        spins = torch.from_numpy(random_sz0_configs(L, B, cfg.get("config_seed", 5))).cuda()
+        for _ in range(args.warmup):
+            r = ctx.correlations(spins, sources)
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.steps):
+            r = ctx.correlations(spins, sources)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1) / max(args.steps, 1)
+        row = {"workload": wl, "samples": B, "sources": len(sources), "ms": ms,
+               "items_per_s": B * len(sources) / (ms / 1e3), "status": ctx.sync_status()[0]}
+        if bulk_sources:
+            row["M2"] = ctx.structure_factor(r["mean"], sources).item()
+        else:
+            row["centre_row"] = [float(x) for x in r["mean"][0].view(L, L)[L // 2].cpu()]
+        rows.append(row)
+        ctx.close()
+    print(json.dumps({"metric": "spin-correlation items (sample, source) per second", "unit": "items/s",
+                      "precision": args.precision, "steps": args.steps, "warmup": args.warmup,
+                      "data": "synthetic", "runs": rows}), flush=True)
+
+
 def main():
     args = parse()
     if args.mode == "contraction":
         run_contraction(args)
+        return
+    if args.mode == "correlations":
+        run_correlations(args)
         return
     cfg = dict(CONFIGS[args.workload])
     if args.impl == "reference":
