@@ -75,12 +75,22 @@ def tuning_key(L, D, Dc, precision):
 class PepsContext:
     """One library context: shape, precision form and device workspace."""
 
-    def __init__(self, L, D, Dc, J1=1.0, J2=0.5, precision="fp64", slots=0):
+    def __init__(self, L, D, Dc, J1=1.0, J2=0.5, precision="fp64", slots=0, variant=None):
+        """variant: compile-time knobs of the fused VMC kernel ({"PEPS_QR_NB":
+        8, ...}, see build.py); that build is made if missing (two
+        translation units) and used by this context.  Default: the tuned
+        variant of tuning.json for this shape, else the default build."""
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required (there is no CPU path)")
         self.torch = torch
-        self.lib = _lib_for(int(L), int(D), int(Dc), precision)
+        if variant:
+            from . import build as B
+            knobs = dict(B.DEFAULTS)
+            knobs.update(variant)
+            self.lib = _lib.load_path(B.build_variant(knobs, precision))
+        else:
+            self.lib = _lib_for(int(L), int(D), int(Dc), precision)
         self.L, self.D, self.Dc = int(L), int(D), int(Dc)
         self.N = self.L * self.L
         self.D4 = self.D ** 4

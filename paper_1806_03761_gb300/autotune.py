@@ -6,9 +6,11 @@ Knobs: PEPS_QR_NB (Householder panel width; it also sets the panel capacity
 of the blocked bidiagonalisation), PEPS_BA_FF / PEPS_BA_F64 (outputs per
 thread along the A-only digit of a contraction), PEPS_MINB (blocks per SM
 the register budget is set for; the default slot count is this many per SM),
-PEPS_NT (threads per block), and two code paths: PEPS_QR_PREFETCH (the next
-trailing column of the blocked QR prefetched into L1) and PEPS_BIDIAG_TPC
-(A'^T v of the bidiagonalisation with one thread per column).  Search: the default, then one knob changed
+PEPS_NT (threads per block), and three code paths: PEPS_QR_PREFETCH (the
+next trailing column of the blocked QR prefetched into L1), PEPS_BIDIAG_TPC
+(A'^T v of the bidiagonalisation with one thread per column) and
+PEPS_QR_TALL_PAIR (panels of 897 to 2048 rows held in the registers of two
+warps per column).  Search: the default, then one knob changed
 at a time (a coordinate step); every candidate library is built (the C ABI
 and the form's fused kernel recompiled, see build.py), then timed in its own
 process on one wave of chains of the shape: one warm-up VMC step and --steps
@@ -32,6 +34,7 @@ CANDIDATES = [
     {"PEPS_QR_PREFETCH": 1},
     {"PEPS_BIDIAG_TPC": 1},
     {"PEPS_QR_PREFETCH": 1, "PEPS_BIDIAG_TPC": 1},
+    {"PEPS_QR_PREFETCH": 1, "PEPS_BIDIAG_TPC": 1, "PEPS_QR_TALL_PAIR": 1},
     {"PEPS_QR_NB": 8},
     {"PEPS_QR_NB": 2},
     {"PEPS_BA_FF": 2, "PEPS_BA_F64": 1},
@@ -102,6 +105,9 @@ def main():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--child", action="store_true")
     ap.add_argument("--write", action="store_true", help="record the winner in tuning.json")
+    ap.add_argument("--only", default="", help="comma-separated candidate numbers to time (default all)")
+    ap.add_argument("--also", default="", help="record the winner also for these shapes, "
+                    "'L,D,Dc;L,D,Dc' (shapes with the same per-site bond matrices)")
     args = ap.parse_args()
     if args.child:
         child(args)
@@ -109,6 +115,8 @@ def main():
     B.build_default()
     import concurrent.futures as cf
     cands = [knobs_of(d) for d in CANDIDATES]
+    if args.only:
+        cands = [cands[int(q)] for q in args.only.split(",")]
     t0 = time.time()
     with cf.ThreadPoolExecutor(max_workers=len(cands)) as ex:
         libs = list(ex.map(lambda k: B.build_variant(k, args.precision), cands))
@@ -134,6 +142,10 @@ def main():
     if args.write:
         table = json.load(open(B.TUNING)) if os.path.exists(B.TUNING) else {}
         table[key] = entry
+        for shp in filter(None, args.also.split(";")):
+            L, D, Dc = (int(x) for x in shp.split(","))
+            other = dict(entry, measured_on=key)
+            table["%dx%d_D%d_Dc%d_%s" % (L, L, D, Dc, args.precision)] = other
         json.dump(table, open(B.TUNING, "w"), indent=1, sort_keys=True)
 
 

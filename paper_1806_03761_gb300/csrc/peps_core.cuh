@@ -331,6 +331,12 @@ __device__ void householder_r_unblocked(R* X, int m, int n, R* Rout, R* sh) {
 #ifndef PEPS_BIDIAG_TPC
 #define PEPS_BIDIAG_TPC 0
 #endif
+// Tall panels (more than PEPS_QR_ROWS rows, up to 2048): the trailing column
+// in the registers of two warps (qr_trailing_pair) instead of two streaming
+// passes of one warp.
+#ifndef PEPS_QR_TALL_PAIR
+#define PEPS_QR_TALL_PAIR 0
+#endif
 #define PEPS_QR_ROWS 896
 
 // Apply the panel's reflectors (explicit vectors v_s, zero above row s and
@@ -409,6 +415,93 @@ __device__ __forceinline__ void qr_trailing(R* X, int m, int n, int k0, int mr, 
   }
 }
 
+// Trailing update of the tall blocked QR with two warps per column: the
+// column's rows k0..m-1 are split between the pair (CAP rows per lane each)
+// and held in registers; each warp forms its half of the nb dot products
+// V^T x and reduces it within the warp; the halves are added through shared
+// memory (xch, 2 NB scalars per pair) under the pair's named barrier, in the
+// same order in both warps; then each warp updates its half and writes it
+// back once: one read and one write of the column per panel.  Both warps of a
+// pair run the same columns, and every iteration meets the barrier twice.
+template <class R, int CAP>
+__device__ __forceinline__ void qr_trailing_pair(R* X, int m, int n, int k0, int nb, int c0,
+                                                 const R* tt, R* xch) {
+  typedef Arith<R> M;
+  const int lane = threadIdx.x % PEPS_WARP, wid = threadIdx.x / PEPS_WARP;
+  const int nw = blockDim.x / PEPS_WARP;
+  const int pair = wid >> 1, half = wid & 1, npairs = nw >> 1;
+  const int mr = m - k0;
+  const int hrows = (mr + 1) >> 1;
+  const int r0 = k0 + half * hrows;                 // first row of this half
+  const int rcount = half ? mr - hrows : hrows;     // its rows
+  R* mine = xch + (pair * 2 + half) * PEPS_QR_NB;
+  const R* lo = xch + (pair * 2) * PEPS_QR_NB;
+  const R* hi = lo + PEPS_QR_NB;
+  for (int c = c0 + pair; c < n; c += npairs) {
+    R* x = X + (int64_t)c * m + r0;
+    R xr[CAP];
+    typename M::acc_t a[PEPS_QR_NB];
+#pragma unroll
+    for (int s = 0; s < PEPS_QR_NB; ++s) M::acc_init(a[s]);
+#pragma unroll
+    for (int q = 0; q < CAP; ++q) {
+      const int ii = lane + q * PEPS_WARP;
+      xr[q] = ii < rcount ? x[ii] : M::zero();
+      if (ii < rcount) {
+        const int i = r0 + ii;
+#pragma unroll
+        for (int s = 0; s < PEPS_QR_NB; ++s)
+          if (s < nb && i >= k0 + s) {
+            const R v = i == k0 + s ? M::one() : X[(int64_t)(k0 + s) * m + i];
+            M::mac(a[s], v, xr[q]);
+          }
+      }
+    }
+    R wv[PEPS_QR_NB];
+#pragma unroll
+    for (int s = 0; s < PEPS_QR_NB; ++s) wv[s] = M::acc_get(a[s]);
+#pragma unroll
+    for (int o = PEPS_WARP / 2; o > 0; o >>= 1) {
+#pragma unroll
+      for (int s = 0; s < PEPS_QR_NB; ++s) wv[s] = wv[s] + shfl_xor_r(wv[s], o);
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int s = 0; s < PEPS_QR_NB; ++s) mine[s] = wv[s];
+    }
+    asm volatile("bar.sync %0, 64;" ::"r"(1 + pair) : "memory");
+    R tot[PEPS_QR_NB];
+#pragma unroll
+    for (int s = 0; s < PEPS_QR_NB; ++s) tot[s] = lo[s] + hi[s];
+    asm volatile("bar.sync %0, 64;" ::"r"(1 + pair) : "memory");
+    R wt[PEPS_QR_NB];
+#pragma unroll
+    for (int s = 0; s < PEPS_QR_NB; ++s) {
+      typename M::acc_t b;
+      M::acc_init(b);
+#pragma unroll
+      for (int r = 0; r <= s; ++r)
+        if (s < nb) M::mac(b, tt[r * PEPS_QR_NB + s], tot[r]);
+      wt[s] = M::acc_get(b);
+    }
+#pragma unroll
+    for (int q = 0; q < CAP; ++q) {
+      const int ii = lane + q * PEPS_WARP;
+      if (ii < rcount) {
+        const int i = r0 + ii;
+        R v = xr[q];
+#pragma unroll
+        for (int s = 0; s < PEPS_QR_NB; ++s)
+          if (s < nb && i >= k0 + s) {
+            const R w = i == k0 + s ? M::one() : X[(int64_t)(k0 + s) * m + i];
+            v = M::sub_mul(v, w, wt[s]);
+          }
+        x[ii] = v;
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Blocked form for panels taller than the register/shared-memory capacity
 // (m > PEPS_QR_ROWS): the panel of PEPS_QR_NB columns is factored in place
@@ -416,11 +509,19 @@ __device__ __forceinline__ void qr_trailing(R* X, int m, int n, int k0, int mr, 
 // x -= V T^T V^T x in two streaming passes per panel (the dot products, then
 // the update), the reflectors read from the panel columns (L1-resident,
 // shared by the warps): three accesses of a trailing element per panel
-// instead of three per reflector.  sh: >= 2 PEPS_QR_NB + 2 PEPS_QR_NB^2
-// scalars of shared memory.
+// instead of three per reflector; with PEPS_QR_TALL_PAIR, up to 2048 rows
+// the column stays in the registers of two warps instead (qr_trailing_pair):
+// one read and one write.
+// sh: >= 2 PEPS_QR_NB + 2 PEPS_QR_NB^2 + (warps) PEPS_QR_NB scalars of
+// shared memory.
 // ---------------------------------------------------------------------------
 template <class R>
-__device__ void householder_r_tall(R* X, int m, int n, R* Rout, R* sh) {
+#if PEPS_QR_TALL_PAIR
+__device__ __noinline__
+#else
+__device__
+#endif
+void householder_r_tall(R* X, int m, int n, R* Rout, R* sh) {
   typedef Arith<R> M;
   const int t = threadIdx.x, lane = t % PEPS_WARP, wid = t / PEPS_WARP;
   const int nw = (blockDim.x + PEPS_WARP - 1) / PEPS_WARP;
@@ -493,7 +594,15 @@ __device__ void householder_r_tall(R* X, int m, int n, R* Rout, R* sh) {
       }
     }
     __syncthreads();
-    // 3. the trailing columns, one warp each, two passes
+    // 3. the trailing columns: two warps per column held in registers while
+    //    the rows fit (up to 2048), else one warp per column in two passes
+#if PEPS_QR_TALL_PAIR
+    if (nw >= 2 && (nw & 1) == 0 && m - k0 <= 2 * PEPS_WARP * 32) {
+      qr_trailing_pair<R, 32>(X, m, n, k0, nb, k0 + nb, tt, g + PEPS_QR_NB * PEPS_QR_NB);
+      __syncthreads();
+      continue;
+    }
+#endif
     for (int c = k0 + nb + wid; c < n; c += nw) {
       R* x = X + (int64_t)c * m;
       typename M::acc_t a[PEPS_QR_NB];

@@ -94,6 +94,10 @@ CONFIGS = {
     # QR and SVD shapes per site): profiling captures
     "12x12_D6_Dc24": dict(L=12, D=6, Dc=24, recipe="gauss", seed=8,
                           config_seed=9, batch=304),
+    # a smaller lattice with the 24x24 workload's bond dimensions (QR panels
+    # of 2048 x 256, 256 x 256 SVDs): tuning and profiling
+    "12x12_D8_Dc32": dict(L=12, D=8, Dc=32, recipe="gauss", seed=10,
+                          config_seed=11, batch=304),
 }
 
 

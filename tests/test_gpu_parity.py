@@ -331,3 +331,25 @@ def test_vmc_step_equals_evaluate_then_sweep(prec):
     assert np.array_equal(fused["accepted"].cpu().numpy(), acc)
     assert ctx.sync_status()[0] == 0
     ctx.close()
+
+
+def test_tall_panel_pair_variant_matches_the_oracle():
+    """The fused VMC kernel built with the two-warp tall-panel QR
+    (PEPS_QR_TALL_PAIR; 6x6, D=8, Dc=32: panels of 2048 x 256): its
+    evaluation of the chains' configurations matches the oracle."""
+    L, D, Dc = 6, 8, 32
+    A = make_peps(L, D, seed=6)
+    spins = random_sz0_configs(L, 2, seed=7)
+    from paper_1806_03761_gb300 import PepsContext
+    c = PepsContext(L, D, Dc, precision="mixed", slots=2,
+                    variant={"PEPS_QR_TALL_PAIR": 1, "PEPS_QR_PREFETCH": 1, "PEPS_BIDIAG_TPC": 1})
+    c.set_tensors(torch.from_numpy(A).cuda())
+    st = torch.from_numpy(spins.copy()).cuda()
+    r = c.vmc_step(5, st, 3)
+    assert c.sync_status()[0] == 0
+    ref = oracle.evaluate_batch(A, spins, L, Dc)
+    e = r["e_loc"].cpu().numpy()
+    assert np.array_equal(r["sign"].cpu().numpy(), ref["sign"].astype(np.int8))
+    assert np.max(np.abs(r["log_abs"].cpu().numpy() - ref["log_abs"])) <= TOL["mixed"]
+    assert np.max(np.abs(e - ref["e_loc"]) / np.maximum(1.0, np.abs(ref["e_loc"]))) <= TOL["mixed"]
+    c.close()
