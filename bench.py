@@ -47,9 +47,9 @@ E2E_MAX_STEPS = 3
 # profiles/ give the command).  Keyed by (workload, precision form); only
 # valid for the kernel the capture was taken from.
 TRAFFIC_PER_CHAIN = {
-    # 32-chain launch: 8.236 GB read + 44.986 GB written
+    # 32-chain launch of the tuned variant: 8.162 GB read + 44.148 GB written
     # (profiles/peps_vmc_16x16_D6_Dc24_mixed_traffic.md)
-    ("16x16_D6_Dc24", "mixed"): (8235538432 + 44985864448) / 32,
+    ("16x16_D6_Dc24", "mixed"): (8162261504 + 44147782144) / 32,
 }
 METRIC = "local-energy samples/s at 16x16 D=6 Dc=24, mixed vs FP64; p50/p99 latency"
 
@@ -293,14 +293,15 @@ def run_serving(args):
         for prec in forms:
             row[prec] = _summary(_serve(P, stream, prec, tensors, warm))
         sweep.append(row)
+        print("rate %.3g/s: %s" % (rate, json.dumps(row)), file=sys.stderr, flush=True)
     coverage = None
     if not args.no_coverage:
         stream = [(0.0, L, D, Dc, 64, 7000 + q) for q, (L, D, Dc) in enumerate(SERVING_SHAPES)]
         tensors = {sd: (mk(L, D, sd % 1000, "gauss"), random_sz0_configs(L, B, sd % 997))
                    for (_, L, D, Dc, B, sd) in stream}
         outs = _serve(P, stream, "mixed", tensors, [])
-        coverage = {"%dx%d D%d Dc%d" % shp[:3]: {"latency_s": o["latency_s"], "status": o["status"]}
-                    for o, shp in outs}
+        coverage = {"%dx%d D%d Dc%d" % (shp[0], shp[0], shp[1], shp[2]):
+                    {"latency_s": o["latency_s"], "status": o["status"]} for o, shp in outs}
     best = max(sweep, key=lambda r: r["mixed"]["value"])
     m = best["mixed"]
     line = {"metric": "serving: local-energy samples/s and p50/p99 request latency, Poisson job mix",
