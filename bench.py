@@ -67,7 +67,8 @@ def parse():
     p.add_argument("--slots", type=int, default=0)
     p.add_argument("--dt", type=float, default=1e-3)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--mode", default="vmc", choices=["vmc", "serving", "contraction", "correlations"],
+    p.add_argument("--mode", default="vmc",
+                   choices=["vmc", "serving", "contraction", "correlations", "multi"],
                    help="serving: a Poisson stream of evaluation jobs through peps_server_*; "
                         "contraction: tensor-core vs CUDA-core column-step contractions")
     p.add_argument("--arrival-s", type=float, default=20.0,
@@ -431,8 +432,78 @@ def run_correlations(args):
                       "data": "synthetic", "runs": rows}), flush=True)
 
 
+MULTI_JOBS = [  # (L, D, Dc, B): jobs of the serving mix's smaller shapes
+    (16, 6, 24, 64), (12, 6, 24, 128), (16, 4, 16, 256), (12, 4, 16, 256), (8, 6, 24, 256),
+    (8, 4, 16, 512), (20, 4, 16, 128), (8, 8, 32, 64)]
+
+
+def run_multi(args):
+    """--mode multi: the local energies of jobs of different shapes (MULTI_JOBS,
+    mixed form), three ways: one persistent launch over all their samples
+    (peps_local_energy_multi: a work queue of (job, sample) items on a pool
+    of two slots per SM), every job's own launches on its own stream at the
+    same time, and the jobs one after another; makespan (CUDA events)."""
+    import torch
+
+    import paper_1806_03761_gb300 as P
+    from synth import make_peps, random_sz0_configs
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    ctxs, spins = [], []
+    for q, (L, D, Dc, B) in enumerate(MULTI_JOBS):
+        c = P.PepsContext(L, D, Dc, precision="mixed", slots=min(B, 2 * sms))
+        c.set_tensors(torch.from_numpy(make_peps(L, D, 300 + q)).cuda())
+        ctxs.append(c)
+        spins.append(torch.from_numpy(random_sz0_configs(L, B, 400 + q)).cuda())
+    pool = P.PepsPool([j[:3] for j in MULTI_JOBS], precision="mixed", slots=2 * sms,
+                      max_jobs=len(MULTI_JOBS))
+    jobs = list(zip(ctxs, spins))
+    main = torch.cuda.current_stream()
+    streams = [torch.cuda.Stream() for _ in jobs]
+
+    def one_launch():
+        pool.local_energy(jobs)
+
+    def concurrent():
+        for (c, sp), st in zip(jobs, streams):
+            st.wait_stream(main)
+            with torch.cuda.stream(st):
+                c.local_energy(sp)
+        for st in streams:
+            main.wait_stream(st)
+
+    def sequential():
+        for c, sp in jobs:
+            c.local_energy(sp)
+
+    res = {}
+    for name, fn in (("one_launch", one_launch), ("concurrent_streams", concurrent),
+                     ("sequential", sequential)):
+        for _ in range(max(args.warmup, 1)):
+            fn()
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(main)
+        for _ in range(args.steps):
+            fn()
+        t1.record(main)
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1) / max(args.steps, 1)
+        res[name] = {"ms": ms, "samples_per_s": sum(j[3] for j in MULTI_JOBS) / (ms / 1e3)}
+    res["pool_status"] = pool.sync_status()[0]
+    pool.close()
+    for c in ctxs:
+        c.close()
+    print(json.dumps({"metric": "makespan of a batch of jobs of different shapes (local energies)",
+                      "unit": "ms", "jobs": [list(j) for j in MULTI_JOBS], "precision": "mixed",
+                      "steps": args.steps, "warmup": args.warmup, "data": "synthetic",
+                      "results": res}), flush=True)
+
+
 def main():
     args = parse()
+    if args.mode == "multi":
+        run_multi(args)
+        return
     if args.mode == "contraction":
         run_contraction(args)
         return
