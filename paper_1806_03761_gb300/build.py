@@ -121,8 +121,12 @@ def tuned_variants():
 def build(verbose=False, force=False):
     """Compile and link libpeps.so and the tuned variants; returns its path."""
     lib = build_default(verbose, force)
+    todo = {}
     for knobs, prec in tuned_variants():
-        build_variant(knobs, prec, verbose)
+        todo.setdefault(variant_tag(knobs, prec), (knobs, prec))
+    if todo:
+        with cf.ThreadPoolExecutor(max_workers=len(todo)) as ex:
+            list(ex.map(lambda kp: build_variant(kp[0], kp[1], verbose), todo.values()))
     return lib
 
 
