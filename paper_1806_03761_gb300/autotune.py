@@ -6,11 +6,13 @@ Knobs: PEPS_QR_NB (Householder panel width; it also sets the panel capacity
 of the blocked bidiagonalisation), PEPS_BA_FF / PEPS_BA_F64 (outputs per
 thread along the A-only digit of a contraction), PEPS_MINB (blocks per SM
 the register budget is set for; the default slot count is this many per SM),
-PEPS_NT (threads per block), and three code paths: PEPS_QR_PREFETCH (the
-next trailing column of the blocked QR prefetched into L1), PEPS_BIDIAG_TPC
-(A'^T v of the bidiagonalisation with one thread per column) and
-PEPS_QR_TALL_PAIR (panels of 897 to 2048 rows held in the registers of two
-warps per column).  Search: the default, then one knob changed
+PEPS_NT (threads per block), PEPS_BB_FF (outputs per thread along the
+B-only digit), and the code paths PEPS_QR_PREFETCH (the next trailing column
+of the blocked QR prefetched into L1), PEPS_BIDIAG_TPC (A'^T v of the
+bidiagonalisation with one thread per column), PEPS_QR_TALL_PAIR (panels of
+897 to 2048 rows held in the registers of two warps per column),
+PEPS_CTR_PIPE (contraction operands loaded one reduction step ahead) and
+PEPS_QR_ACC (the QR's trailing update as compensated accumulations).  Search: the default, then one knob changed
 at a time (a coordinate step); every candidate library is built (the C ABI
 and the form's fused kernel recompiled, see build.py), then timed in its own
 process on one wave of chains of the shape: one warm-up VMC step and --steps
@@ -40,6 +42,11 @@ CANDIDATES = [
     {"PEPS_BA_FF": 2, "PEPS_BA_F64": 1},
     {"PEPS_MINB": 1, "PEPS_NT": 512},     # one block of 16 warps per SM
     {"PEPS_MINB": 1},                     # one block of 8 warps per SM, 255 registers
+    {"PEPS_QR_PREFETCH": 1, "PEPS_BIDIAG_TPC": 1, "PEPS_CTR_PIPE": 1},
+    {"PEPS_QR_PREFETCH": 1, "PEPS_BIDIAG_TPC": 1, "PEPS_QR_ACC": 1},
+    {"PEPS_QR_PREFETCH": 1, "PEPS_BIDIAG_TPC": 1, "PEPS_CTR_PIPE": 1, "PEPS_QR_ACC": 1},
+    {"PEPS_QR_PREFETCH": 1, "PEPS_BIDIAG_TPC": 1, "PEPS_CTR_PIPE": 1, "PEPS_QR_ACC": 1,
+     "PEPS_BB_FF": 4},
 ]
 
 

@@ -6,8 +6,9 @@ it or any header in csrc/ or include/ is newer than its object.
 
 Tuned variants (paper_1806_03761_gb300/tuning.json, written by the
 autotuner): a variant sets compile-time knobs of the kernels (PEPS_QR_NB,
-PEPS_BA_FF, PEPS_BA_F64, PEPS_MINB, PEPS_NT, and the code paths
-PEPS_QR_PREFETCH, PEPS_BIDIAG_TPC and PEPS_QR_TALL_PAIR).  It recompiles the units those
+PEPS_BA_FF, PEPS_BA_F64, PEPS_BB_FF, PEPS_MINB, PEPS_NT, and the code paths
+PEPS_QR_PREFETCH, PEPS_BIDIAG_TPC, PEPS_QR_TALL_PAIR, PEPS_CTR_PIPE and
+PEPS_QR_ACC).  It recompiles the units those
 knobs reach for one precision form -- the C ABI and the form's fused
 VMC-step kernel -- and links them with the default objects of every other
 unit (device code is compiled per unit, without relocatable device code, so
@@ -57,7 +58,8 @@ def _compile(src, obj, verbose, extra=()):
 
 
 DEFAULTS = {"PEPS_QR_NB": 4, "PEPS_BA_FF": 4, "PEPS_BA_F64": 2, "PEPS_MINB": 2, "PEPS_NT": 256,
-            "PEPS_QR_PREFETCH": 0, "PEPS_BIDIAG_TPC": 0, "PEPS_QR_TALL_PAIR": 0}
+            "PEPS_QR_PREFETCH": 0, "PEPS_BIDIAG_TPC": 0, "PEPS_QR_TALL_PAIR": 0,
+            "PEPS_BB_FF": 2, "PEPS_CTR_PIPE": 0, "PEPS_QR_ACC": 0}
 FORMS = {"fp64": "f64", "mixed": "ff", "fp32": "f32"}
 TUNING = os.path.join(PKG, "tuning.json")
 

@@ -88,6 +88,9 @@ template <> struct Arith<double> {
   PEPS_HD static void acc_init(acc_t& a) { a = 0.0; }
   PEPS_HD static void mac(acc_t& a, double x, double y) { a = fma(x, y, a); }
   PEPS_HD static double acc_get(const acc_t& a) { return a; }
+  PEPS_HD static void acc_set(acc_t& a, double x) { a = x; }
+  // a += the accumulator of lane (this lane ^ o)
+  PEPS_HD static void acc_shfl_add(acc_t& a, int o) { a = a + __shfl_xor_sync(0xffffffffu, a, o); }
   // x - v w in one rounding
   PEPS_HD static double sub_mul(double x, double v, double w) { return fma(-v, w, x); }
   PEPS_HD static double sqrt_(double x) { return sqrt(x); }
@@ -106,6 +109,8 @@ template <> struct Arith<float> {
   PEPS_HD static void acc_init(acc_t& a) { a = 0.0f; }
   PEPS_HD static void mac(acc_t& a, float x, float y) { a = fmaf(x, y, a); }
   PEPS_HD static float acc_get(const acc_t& a) { return a; }
+  PEPS_HD static void acc_set(acc_t& a, float x) { a = x; }
+  PEPS_HD static void acc_shfl_add(acc_t& a, int o) { a = a + __shfl_xor_sync(0xffffffffu, a, o); }
   PEPS_HD static float sub_mul(float x, float v, float w) { return fmaf(-v, w, x); }
   PEPS_HD static float sqrt_(float x) { return sqrtf(x); }
   PEPS_HD static float scale(float x, double s) { return x * (float)s; }
@@ -136,6 +141,17 @@ template <> struct Arith<ff> {
     a.c = __fadd_rn(a.c, __fadd_rn(t.lo, e));
   }
   PEPS_HD static ff acc_get(const acc_t& a) { return ff_fast_two_sum(a.s, a.c); }
+  PEPS_HD static void acc_set(acc_t& a, ff x) { a.s = x.hi; a.c = x.lo; }
+  // merge with the accumulator of lane (this lane ^ o): TwoSum of the two
+  // leading sums, their error and both correction terms into c (commutative,
+  // so both lanes of a pair end with the same value)
+  PEPS_HD static void acc_shfl_add(acc_t& a, int o) {
+    const float s2 = __shfl_xor_sync(0xffffffffu, a.s, o);
+    const float c2 = __shfl_xor_sync(0xffffffffu, a.c, o);
+    const ff t = ff_two_sum(a.s, s2);
+    a.s = t.hi;
+    a.c = __fadd_rn(__fadd_rn(a.c, c2), t.lo);
+  }
   // x - v w: the high parts of x and of the exact product v.hi w.hi meet in
   // one TwoSum; the product's rounding error (FMA), its cross terms and the
   // low parts are summed in FP32 and renormalised (error a few 2^-48 of

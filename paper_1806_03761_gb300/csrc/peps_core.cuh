@@ -87,8 +87,8 @@ __device__ __forceinline__ Ctr ctr_init() {
 // read through the coherent path (no __restrict__ / read-only cache).
 //
 // Register blocking: when the output has a digit carried only by A (dA) and
-// one carried only by B (dB), each thread computes a BA x 2 block of outputs
-// over those digits, so that every loaded element of A feeds two and every
+// one carried only by B (dB), each thread computes a BA x BB block of outputs
+// over those digits, so that every loaded element of A feeds BB and every
 // loaded element of B BA multiply-adds (the summation order of each output
 // is unchanged).  Otherwise each thread computes two
 // outputs adjacent in the fastest digit (shared loads where an operand does
@@ -102,8 +102,21 @@ __device__ __forceinline__ Ctr ctr_init() {
 #ifndef PEPS_BA_F64
 #define PEPS_BA_F64 2
 #endif
-template <class R> struct ContractBlock { static constexpr int BA = PEPS_BA_FF; };
-template <> struct ContractBlock<double> { static constexpr int BA = PEPS_BA_F64; };
+// Outputs per thread along the B-only digit: PEPS_BB_FF (default 2) for the
+// FP32-word forms, 2 for FP64.
+#ifndef PEPS_BB_FF
+#define PEPS_BB_FF 2
+#endif
+// PEPS_CTR_PIPE=1: the operands of reduction step t + 1 are loaded before
+// the multiply-adds of step t, so that their latency overlaps the arithmetic
+// (the same products summed in the same order: bit-identical results).
+#ifndef PEPS_CTR_PIPE
+#define PEPS_CTR_PIPE 0
+#endif
+template <class R> struct ContractBlock {
+  static constexpr int BA = PEPS_BA_FF, BB = PEPS_BB_FF;
+};
+template <> struct ContractBlock<double> { static constexpr int BA = PEPS_BA_F64, BB = 2; };
 
 template <class R>
 __device__ void contract(const Ctr& d, const R* A, const R* B, R* C) {
@@ -116,7 +129,7 @@ __device__ void contract(const Ctr& d, const R* A, const R* B, R* C) {
   }
   if (dA >= 0 && dB >= 0) {
     // BA x BB outputs per thread over (dA, dB)
-    constexpr int BA = ContractBlock<R>::BA, BB = 2;
+    constexpr int BA = ContractBlock<R>::BA, BB = ContractBlock<R>::BB;
     int eb[5];
     int tot = 1;
     int sA = 0, sB = 0, cA = 0, cB = 0, nA = 1, nB = 1;
@@ -151,6 +164,44 @@ __device__ void contract(const Ctr& d, const R* A, const R* B, R* C) {
       for (int x = 0; x < BA; ++x)
 #pragma unroll
         for (int y = 0; y < BB; ++y) M::acc_init(c[x][y]);
+#if PEPS_CTR_PIPE
+      // reduction steps t = k1 * k2-extent + k2 in order; offsets of step t
+      // in fa/fb, the next step's operands loaded ahead (the last step
+      // reloads its own, in range)
+      const int K2 = d.k2, KT = d.k1 * d.k2;
+      if (KT > 0) {
+        int fa = oa, fb = ob, k2 = 0;
+        R av[BA], bv[BB];
+#pragma unroll
+        for (int x = 0; x < BA; ++x) av[x] = A[fa + da[x]];
+#pragma unroll
+        for (int y = 0; y < BB; ++y) bv[y] = B[fb + db[y]];
+        for (int t = 0; t < KT; ++t) {
+          int ga = fa + d.ka2, gb = fb + d.kb2;
+          if (++k2 == K2) {
+            k2 = 0;
+            ga += d.ka1 - K2 * d.ka2;
+            gb += d.kb1 - K2 * d.kb2;
+          }
+          if (t + 1 == KT) { ga = fa; gb = fb; }
+          R an[BA], bn[BB];
+#pragma unroll
+          for (int x = 0; x < BA; ++x) an[x] = A[ga + da[x]];
+#pragma unroll
+          for (int y = 0; y < BB; ++y) bn[y] = B[gb + db[y]];
+#pragma unroll
+          for (int x = 0; x < BA; ++x)
+#pragma unroll
+            for (int y = 0; y < BB; ++y) M::mac(c[x][y], av[x], bv[y]);
+#pragma unroll
+          for (int x = 0; x < BA; ++x) av[x] = an[x];
+#pragma unroll
+          for (int y = 0; y < BB; ++y) bv[y] = bn[y];
+          fa = ga;
+          fb = gb;
+        }
+      }
+#else
       for (int k1 = 0; k1 < d.k1; ++k1) {
         const R* pa = A + oa + k1 * d.ka1;
         const R* pb = B + ob + k1 * d.kb1;
@@ -166,6 +217,7 @@ __device__ void contract(const Ctr& d, const R* A, const R* B, R* C) {
             for (int y = 0; y < BB; ++y) M::mac(c[x][y], av[x], bv[y]);
         }
       }
+#endif
 #pragma unroll
       for (int x = 0; x < BA; ++x)
 #pragma unroll
@@ -194,6 +246,32 @@ __device__ void contract(const Ctr& d, const R* A, const R* B, R* C) {
     typename M::acc_t acc0, acc1;
     M::acc_init(acc0);
     M::acc_init(acc1);
+#if PEPS_CTR_PIPE
+    const int K2 = d.k2, KT = d.k1 * d.k2;
+    if (KT > 0) {
+      int fa = oa, fb = ob, k2 = 0;
+      R a0 = A[fa], b0 = B[fb];
+      R a1 = da ? A[fa + da] : a0;
+      R b1 = db ? B[fb + db] : b0;
+      for (int t = 0; t < KT; ++t) {
+        int ga = fa + d.ka2, gb = fb + d.kb2;
+        if (++k2 == K2) {
+          k2 = 0;
+          ga += d.ka1 - K2 * d.ka2;
+          gb += d.kb1 - K2 * d.kb2;
+        }
+        if (t + 1 == KT) { ga = fa; gb = fb; }
+        const R na0 = A[ga], nb0 = B[gb];
+        const R na1 = da ? A[ga + da] : na0;
+        const R nb1 = db ? B[gb + db] : nb0;
+        M::mac(acc0, a0, b0);
+        M::mac(acc1, a1, b1);
+        a0 = na0; b0 = nb0; a1 = na1; b1 = nb1;
+        fa = ga;
+        fb = gb;
+      }
+    }
+#else
     for (int k1 = 0; k1 < d.k1; ++k1) {
       const R* pa = A + oa + k1 * d.ka1;
       const R* pb = B + ob + k1 * d.kb1;
@@ -205,6 +283,7 @@ __device__ void contract(const Ctr& d, const R* A, const R* B, R* C) {
         M::mac(acc1, a1, b1);
       }
     }
+#endif
     C[oc] = M::acc_get(acc0);
     if (two) C[oc + sc4] = M::acc_get(acc1);
   }
@@ -339,6 +418,14 @@ __device__ void householder_r_unblocked(R* X, int m, int n, R* Rout, R* sh) {
 #endif
 #define PEPS_QR_ROWS 896
 
+// PEPS_QR_ACC=1: the trailing update's warp reductions merge the lanes'
+// compensated accumulators directly, and x - V w' is one compensated
+// accumulation per element (float-float: fewer FP32 operations at the same
+// error bound, a few 2^-48 of |x| + |V w'|; FP64: bit-identical).
+#ifndef PEPS_QR_ACC
+#define PEPS_QR_ACC 0
+#endif
+
 // Apply the panel's reflectors (explicit vectors v_s, zero above row s and
 // one at row s, in vsh with stride PEPS_QR_ROWS) to the trailing columns
 // c0..n-1 of X, rows k0..k0+mr-1, in the compact WY form
@@ -382,6 +469,16 @@ __device__ __forceinline__ void qr_trailing(R* X, int m, int n, int k0, int mr, 
       }
     }
     R wv[PEPS_QR_NB];
+#if PEPS_QR_ACC
+    // the lanes' accumulators merged as accumulators (FP64: the same sums)
+#pragma unroll
+    for (int o = PEPS_WARP / 2; o > 0; o >>= 1) {
+#pragma unroll
+      for (int s = 0; s < PEPS_QR_NB; ++s) M::acc_shfl_add(a[s], o);
+    }
+#pragma unroll
+    for (int s = 0; s < PEPS_QR_NB; ++s) wv[s] = M::acc_get(a[s]);
+#else
 #pragma unroll
     for (int s = 0; s < PEPS_QR_NB; ++s) wv[s] = M::acc_get(a[s]);
 #pragma unroll
@@ -389,6 +486,7 @@ __device__ __forceinline__ void qr_trailing(R* X, int m, int n, int k0, int mr, 
 #pragma unroll
       for (int s = 0; s < PEPS_QR_NB; ++s) wv[s] = wv[s] + shfl_xor_r(wv[s], o);
     }
+#endif
     // w' = T^T w
     R wt[PEPS_QR_NB];
 #pragma unroll
@@ -401,6 +499,24 @@ __device__ __forceinline__ void qr_trailing(R* X, int m, int n, int k0, int mr, 
       wt[s] = M::acc_get(b);
     }
     // x -= V w'
+#if PEPS_QR_ACC
+    // x - sum_s v_s w'_s in one compensated accumulation started at x (FP64:
+    // the same fused multiply-adds as the chain of x - v w below)
+#pragma unroll
+    for (int s = 0; s < PEPS_QR_NB; ++s) wt[s] = -wt[s];
+#pragma unroll
+    for (int q = 0; q < CAP; ++q) {
+      const int i = lane + q * PEPS_WARP;
+      if (i < mr) {
+        typename M::acc_t u;
+        M::acc_set(u, xr[q]);
+#pragma unroll
+        for (int s = 0; s < PEPS_QR_NB; ++s)
+          if (s < nb) M::mac(u, vsh[s * PEPS_QR_ROWS + i], wt[s]);
+        x[i] = M::acc_get(u);
+      }
+    }
+#else
 #pragma unroll
     for (int q = 0; q < CAP; ++q) {
       const int i = lane + q * PEPS_WARP;
@@ -412,6 +528,7 @@ __device__ __forceinline__ void qr_trailing(R* X, int m, int n, int k0, int mr, 
         x[i] = v;
       }
     }
+#endif
   }
 }
 

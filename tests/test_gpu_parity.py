@@ -353,3 +353,59 @@ def test_tall_panel_pair_variant_matches_the_oracle():
     assert np.max(np.abs(r["log_abs"].cpu().numpy() - ref["log_abs"])) <= TOL["mixed"]
     assert np.max(np.abs(e - ref["e_loc"]) / np.maximum(1.0, np.abs(ref["e_loc"]))) <= TOL["mixed"]
     c.close()
+
+
+def _vmc_outputs(ctx, A, spins):
+    ctx.set_tensors(torch.from_numpy(A).cuda())
+    st = torch.from_numpy(spins.copy()).cuda()
+    r = ctx.vmc_step(5, st, 3)
+    assert ctx.sync_status()[0] == 0
+    out = {k: v.cpu().numpy().copy() for k, v in r.items() if hasattr(v, "cpu")}
+    out["state"] = st.cpu().numpy().copy()
+    return out
+
+
+@pytest.mark.parametrize("prec,base", [
+    ("fp64", {}),
+    ("mixed", {"PEPS_QR_PREFETCH": 1, "PEPS_BIDIAG_TPC": 1}),
+])
+def test_pipelined_contraction_is_bit_identical(prec, base):
+    """PEPS_CTR_PIPE loads the next reduction step's operands ahead of the
+    multiply-adds: every product and sum is the same, so the fused step's
+    outputs equal those of the build without it bit for bit (8x8, D=4,
+    Dc=16: every contraction shape of the strips and the absorption; FP64
+    also with PEPS_QR_ACC, the same fused multiply-adds in FP64)."""
+    from paper_1806_03761_gb300 import PepsContext
+    L, D, Dc = 8, 4, 16
+    A = make_peps(L, D, seed=81)
+    spins = random_sz0_configs(L, 6, seed=82)
+    ref = _vmc_outputs(PepsContext(L, D, Dc, precision=prec, slots=3, variant=base or None), A, spins)
+    knobs = dict(base, PEPS_CTR_PIPE=1)
+    if prec == "fp64":
+        knobs["PEPS_QR_ACC"] = 1
+    got = _vmc_outputs(PepsContext(L, D, Dc, precision=prec, slots=3, variant=knobs), A, spins)
+    assert set(ref) == set(got)
+    for k in ref:
+        assert np.array_equal(ref[k], got[k]), k
+
+
+def test_compensated_qr_update_matches_the_oracle():
+    """PEPS_QR_ACC in the float-float form (the trailing update of the
+    blocked QR as one compensated accumulation per element, the warp
+    reductions on the accumulators), with the pipelined contractions and the
+    wider register block: the fused step's evaluation matches the oracle at
+    8x8, D=4, Dc=16 (QR panels of 256 rows) and 6x6, D=6, Dc=24 (864)."""
+    from paper_1806_03761_gb300 import PepsContext
+    knobs = {"PEPS_QR_PREFETCH": 1, "PEPS_BIDIAG_TPC": 1, "PEPS_CTR_PIPE": 1, "PEPS_QR_ACC": 1,
+             "PEPS_BB_FF": 4}
+    for (L, D, Dc, seed) in [(8, 4, 16, 83), (6, 6, 24, 85)]:
+        A = make_peps(L, D, seed=seed)
+        spins = random_sz0_configs(L, 3, seed=seed + 1)
+        c = PepsContext(L, D, Dc, precision="mixed", slots=3, variant=knobs)
+        r = _vmc_outputs(c, A, spins)
+        c.close()
+        ref = oracle.evaluate_batch(A, spins, L, Dc)
+        assert np.array_equal(r["sign"], ref["sign"].astype(np.int8))
+        assert np.max(np.abs(r["log_abs"] - ref["log_abs"])) <= TOL["mixed"]
+        assert np.max(np.abs(r["e_loc"] - ref["e_loc"]) /
+                      np.maximum(1.0, np.abs(ref["e_loc"]))) <= TOL["mixed"]
