@@ -47,6 +47,10 @@ CANDIDATES = [
     {"PEPS_QR_PREFETCH": 1, "PEPS_BIDIAG_TPC": 1, "PEPS_CTR_PIPE": 1, "PEPS_QR_ACC": 1},
     {"PEPS_QR_PREFETCH": 1, "PEPS_BIDIAG_TPC": 1, "PEPS_CTR_PIPE": 1, "PEPS_QR_ACC": 1,
      "PEPS_BB_FF": 4},
+    {"PEPS_QR_PREFETCH": 1, "PEPS_BIDIAG_TPC": 1, "PEPS_QR_TALL_PAIR": 1, "PEPS_CTR_PIPE": 1,
+     "PEPS_QR_ACC": 1},
+    {"PEPS_QR_PREFETCH": 1, "PEPS_BIDIAG_TPC": 1, "PEPS_CTR_PIPE": 1, "PEPS_QR_ACC": 1,
+     "PEPS_MINB": 3},                     # three blocks of 8 warps per SM, 80 registers
 ]
 
 

@@ -575,6 +575,15 @@ __device__ __forceinline__ void qr_trailing_pair(R* X, int m, int n, int k0, int
       }
     }
     R wv[PEPS_QR_NB];
+#if PEPS_QR_ACC
+#pragma unroll
+    for (int o = PEPS_WARP / 2; o > 0; o >>= 1) {
+#pragma unroll
+      for (int s = 0; s < PEPS_QR_NB; ++s) M::acc_shfl_add(a[s], o);
+    }
+#pragma unroll
+    for (int s = 0; s < PEPS_QR_NB; ++s) wv[s] = M::acc_get(a[s]);
+#else
 #pragma unroll
     for (int s = 0; s < PEPS_QR_NB; ++s) wv[s] = M::acc_get(a[s]);
 #pragma unroll
@@ -582,6 +591,7 @@ __device__ __forceinline__ void qr_trailing_pair(R* X, int m, int n, int k0, int
 #pragma unroll
       for (int s = 0; s < PEPS_QR_NB; ++s) wv[s] = wv[s] + shfl_xor_r(wv[s], o);
     }
+#endif
     if (lane == 0) {
 #pragma unroll
       for (int s = 0; s < PEPS_QR_NB; ++s) mine[s] = wv[s];
@@ -601,6 +611,26 @@ __device__ __forceinline__ void qr_trailing_pair(R* X, int m, int n, int k0, int
         if (s < nb) M::mac(b, tt[r * PEPS_QR_NB + s], tot[r]);
       wt[s] = M::acc_get(b);
     }
+#if PEPS_QR_ACC
+#pragma unroll
+    for (int s = 0; s < PEPS_QR_NB; ++s) wt[s] = -wt[s];
+#pragma unroll
+    for (int q = 0; q < CAP; ++q) {
+      const int ii = lane + q * PEPS_WARP;
+      if (ii < rcount) {
+        const int i = r0 + ii;
+        typename M::acc_t u;
+        M::acc_set(u, xr[q]);
+#pragma unroll
+        for (int s = 0; s < PEPS_QR_NB; ++s)
+          if (s < nb && i >= k0 + s) {
+            const R w = i == k0 + s ? M::one() : X[(int64_t)(k0 + s) * m + i];
+            M::mac(u, w, wt[s]);
+          }
+        x[ii] = M::acc_get(u);
+      }
+    }
+#else
 #pragma unroll
     for (int q = 0; q < CAP; ++q) {
       const int ii = lane + q * PEPS_WARP;
@@ -616,6 +646,7 @@ __device__ __forceinline__ void qr_trailing_pair(R* X, int m, int n, int k0, int
         x[ii] = v;
       }
     }
+#endif
   }
 }
 

@@ -409,3 +409,23 @@ def test_compensated_qr_update_matches_the_oracle():
         assert np.max(np.abs(r["log_abs"] - ref["log_abs"])) <= TOL["mixed"]
         assert np.max(np.abs(r["e_loc"] - ref["e_loc"]) /
                       np.maximum(1.0, np.abs(ref["e_loc"]))) <= TOL["mixed"]
+
+
+def test_compensated_tall_pair_update_matches_the_oracle():
+    """PEPS_QR_ACC with the two-warp tall-panel QR (6x6, D=8, Dc=32: panels
+    of 2048 x 256), float-float: the fused step's evaluation matches the
+    oracle."""
+    from paper_1806_03761_gb300 import PepsContext
+    L, D, Dc = 6, 8, 32
+    A = make_peps(L, D, seed=6)
+    spins = random_sz0_configs(L, 2, seed=7)
+    knobs = {"PEPS_QR_TALL_PAIR": 1, "PEPS_QR_PREFETCH": 1, "PEPS_BIDIAG_TPC": 1,
+             "PEPS_CTR_PIPE": 1, "PEPS_QR_ACC": 1}
+    c = PepsContext(L, D, Dc, precision="mixed", slots=2, variant=knobs)
+    r = _vmc_outputs(c, A, spins)
+    c.close()
+    ref = oracle.evaluate_batch(A, spins, L, Dc)
+    assert np.array_equal(r["sign"], ref["sign"].astype(np.int8))
+    assert np.max(np.abs(r["log_abs"] - ref["log_abs"])) <= TOL["mixed"]
+    assert np.max(np.abs(r["e_loc"] - ref["e_loc"]) /
+                  np.maximum(1.0, np.abs(ref["e_loc"]))) <= TOL["mixed"]
