@@ -379,6 +379,22 @@ int peps_sync_status(peps_ctx* ctx, void* stream, int32_t* flags);
  * Host call for roofline reporting; 0 for an invalid shape or `what`. */
 double peps_flops_per_sample(const peps_shape* shape, int32_t what);
 
+/* Per-phase cycle counters of the fused VMC-step kernel (peps_vmc_step) of
+ * ctx's precision form, the counterpart of the paper's hardware-counter
+ * measurement (Sec. "Performance Measurement").  Only a library built with
+ * the compile-time knob PEPS_PHASES=1 counts: thread 0 of every block adds
+ * the clock64() cycles of each phase (summed over blocks and launches since
+ * the last call).  Copies min(n, *n_phases) counters to out (host array),
+ * clears them and sets *n_phases to the number of phases (0 for a build
+ * without the counters).  Phase order: evaluation, sweep, compressions, QR
+ * R factors, QR before an SVD, truncated SVDs, one-row strip environments,
+ * horizontal ratios, B tensors, two-row strip environments, vertical and
+ * diagonal ratios, sweep horizontal moves, sweep two-row right
+ * environments, sweep vertical moves (the first two contain the others,
+ * compressions contain the three after them).  Synchronises the device.
+ * PEPS_EINVAL for a null ctx or n_phases, n < 0, or n > 0 with a null out. */
+int peps_phase_cycles(const peps_ctx* ctx, uint64_t* out, int32_t n, int32_t* n_phases);
+
 /* ------------------------------------------------------------------------
  * Serving: a request loop with continuous batching.  The paper runs one
  * large job; serving many independent VMC users at once has no counterpart

@@ -313,6 +313,18 @@ class PepsContext:
             self._check(rc)
         return rc, f.value
 
+    PHASES = ("eval", "sweep", "compress", "qr", "svd_qr", "svd", "strip1", "ratio_h", "btens",
+              "strip2", "ratio_2", "sweep_h", "sweep_r2", "sweep_v")
+
+    def phase_cycles(self):
+        """Per-phase clock64 cycles of the fused VMC kernel summed over blocks
+        since the last call (peps_phase_cycles), as {phase: cycles}; empty
+        unless this context's library was built with PEPS_PHASES=1."""
+        buf = (ctypes.c_uint64 * len(self.PHASES))()
+        n = ctypes.c_int32(0)
+        self._check(self.lib.peps_phase_cycles(self.h, buf, len(self.PHASES), ctypes.byref(n)))
+        return {self.PHASES[i]: int(buf[i]) for i in range(min(n.value, len(self.PHASES)))}
+
 
 class PepsServer:
     """Serving loop with continuous batching (peps_server_*): evaluation jobs

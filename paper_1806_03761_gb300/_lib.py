@@ -31,7 +31,8 @@ EXPORTS = ("peps_create", "peps_destroy", "peps_last_error", "peps_workspace_byt
            "peps_correlations", "peps_structure_factor", "peps_tc_workspace_bytes", "peps_tc_gemm",
            "peps_cc_workspace_bytes", "peps_cc_gemm", "peps_pool_create", "peps_pool_destroy",
            "peps_pool_slots", "peps_local_energy_multi", "peps_pool_sync_status",
-           "peps_vmc_step_dc", "peps_grad_step_dc", "peps_counters_advance", "peps_vmc_step_host")
+           "peps_vmc_step_dc", "peps_grad_step_dc", "peps_counters_advance", "peps_vmc_step_host",
+           "peps_phase_cycles")
 
 
 class PepsShape(ctypes.Structure):
@@ -74,6 +75,7 @@ _SIGS = {
     "peps_last_error": (ctypes.c_char_p, [P]),
     "peps_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(PepsShape), I32]),
     "peps_slots": (I32, [P, ctypes.POINTER(I32)]),
+    "peps_phase_cycles": (I32, [P, ctypes.POINTER(ctypes.c_uint64), I32, ctypes.POINTER(I32)]),
     "peps_set_tensors": (I32, [P, P, P]),
     "peps_amplitudes": (I32, [P, P, I64, P, P, P]),
     "peps_local_energy": (I32, [P, P, I64, P, P, P, P, P, P]),

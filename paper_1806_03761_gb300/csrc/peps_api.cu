@@ -283,6 +283,15 @@ int peps_slots(const peps_ctx* c, int32_t* slots) {
   return PEPS_OK;
 }
 
+int peps_phase_cycles(const peps_ctx* c, uint64_t* out, int32_t n, int32_t* n_phases) {
+  if (!c || !n_phases || n < 0 || (n > 0 && !out)) return PEPS_EINVAL;
+  unsigned long long* o = reinterpret_cast<unsigned long long*>(out);
+  *n_phases = c->shape.precision == PEPS_FP64 ? peps_phase_read_f64(o, n)
+              : c->shape.precision == PEPS_FP32 ? peps_phase_read_f32(o, n)
+                                                : peps_phase_read_ff(o, n);
+  return PEPS_OK;
+}
+
 int peps_create(const peps_shape* shape, int32_t slots, peps_ctx** out) {
   if (!out) return PEPS_EINVAL;
   *out = nullptr;

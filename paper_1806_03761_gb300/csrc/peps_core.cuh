@@ -8,6 +8,7 @@
 #pragma once
 #include "peps_arith.cuh"
 #include "peps_plan.h"
+#include "peps_trace.cuh"
 
 #ifndef PEPS_NT
 #define PEPS_NT 256          // threads per block

@@ -294,7 +294,9 @@ __device__ __forceinline__ void evaluate_one(const EvalArgs<R>& a, int64_t b, Bl
     EnvDims Ud = env_dims(P, a.steps, i - 1);
     const R* Dn = w.dn + (int64_t)(i + 1) * P.env_cap;
     EnvDims Dd = env_dims(P, a.steps, (i + 1 <= L - 1) ? (L - 2 - i) : -1);
+    PEPS_TIC(t_s1);
     strip1_build<R>(P, i, sp, a.As, U, Ud, Dn, Dd, w, cl1, cr1);
+    PEPS_TOC(t_s1, PH_STRIP1);
     double wv = Arith<R>::to(w.l1[(int64_t)L * P.site_cap]);
     double logw = log(fabs(wv)) + cl1[L] + uplog[ucur] + dnlog[i + 1];
     if (i == 0) {
@@ -310,7 +312,9 @@ __device__ __forceinline__ void evaluate_one(const EvalArgs<R>& a, int64_t b, Bl
       for (int j = 0; j + 1 < L; ++j) {
         int m = i * L + j;
         if (sp[m] == sp[m + 1]) continue;
+        PEPS_TIC(t_rh);
         double r = ratio_h<R>(P, i, j, sp, a.As, U, Ud, Dn, Dd, w, cl1);
+        PEPS_TOC(t_rh, PH_RATIO_H);
         e += P.J1 * 0.5 * r;
         if (threadIdx.x == 0) {
           if (rout) rout[i * (L - 1) + j] = r;
@@ -319,6 +323,7 @@ __device__ __forceinline__ void evaluate_one(const EvalArgs<R>& a, int64_t b, Bl
       }
     }
     if (a.want_delta) {
+      PEPS_TIC(t_bt);
       for (int j = 0; j < L; ++j) {
         int m = i * L + j;
         Col1 k = col_dims(P, Ud, Dd, j);
@@ -332,11 +337,15 @@ __device__ __forceinline__ void evaluate_one(const EvalArgs<R>& a, int64_t b, Bl
           w.delta[(int64_t)m * D4 + o] = Arith<R>::to(Bt[o]) * f;
         __syncthreads();
       }
+      PEPS_TOC(t_bt, PH_BTENS);
     }
     if (a.want_energy && i + 1 < L) {
       const R* Dn2 = w.dn + (int64_t)(i + 2) * P.env_cap;
       EnvDims Dd2 = env_dims(P, a.steps, (i + 2 <= L - 1) ? (L - 3 - i) : -1);
+      PEPS_TIC(t_s2);
       strip2_build<R>(P, i, sp, a.As, U, Ud, Dn2, Dd2, w, cl2);
+      PEPS_TOC(t_s2, PH_STRIP2);
+      PEPS_TIC(t_r2);
       for (int j = 0; j < L; ++j) {
         int m1 = i * L + j, m2 = m1 + L;
         if (sp[m1] != sp[m2]) {
@@ -358,6 +367,7 @@ __device__ __forceinline__ void evaluate_one(const EvalArgs<R>& a, int64_t b, Bl
           }
         }
       }
+      PEPS_TOC(t_r2, PH_RATIO_2);
     }
     // U_i for the next row
     if (i + 1 < L) {

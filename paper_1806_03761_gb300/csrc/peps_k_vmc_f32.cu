@@ -7,3 +7,5 @@ cudaError_t peps_launch_vmc_f32(const EvalArgs<float>& a, const SampleArgs<float
   peps_vmc_kernel<float><<<grid, PEPS_NT, 0, st>>>(a, s);
   return cudaGetLastError();
 }
+
+PEPS_PHASE_READER(peps_phase_read_f32)

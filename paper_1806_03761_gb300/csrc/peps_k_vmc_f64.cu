@@ -7,3 +7,5 @@ cudaError_t peps_launch_vmc_f64(const EvalArgs<double>& a, const SampleArgs<doub
   peps_vmc_kernel<double><<<grid, PEPS_NT, 0, st>>>(a, s);
   return cudaGetLastError();
 }
+
+PEPS_PHASE_READER(peps_phase_read_f64)

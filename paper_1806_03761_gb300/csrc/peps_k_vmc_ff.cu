@@ -7,3 +7,5 @@ cudaError_t peps_launch_vmc_ff(const EvalArgs<ff>& a, const SampleArgs<ff>& s, i
   peps_vmc_kernel<ff><<<grid, PEPS_NT, 0, st>>>(a, s);
   return cudaGetLastError();
 }
+
+PEPS_PHASE_READER(peps_phase_read_ff)

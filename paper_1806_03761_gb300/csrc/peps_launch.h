@@ -19,6 +19,10 @@ cudaError_t peps_launch_sample_f32(const SampleArgs<float>& a, int grid, cudaStr
 cudaError_t peps_launch_vmc_f64(const EvalArgs<double>& a, const SampleArgs<double>& s, int grid, cudaStream_t st);
 cudaError_t peps_launch_vmc_ff(const EvalArgs<ff>& a, const SampleArgs<ff>& s, int grid, cudaStream_t st);
 cudaError_t peps_launch_vmc_f32(const EvalArgs<float>& a, const SampleArgs<float>& s, int grid, cudaStream_t st);
+// per-phase cycle counters of the fused kernel (PEPS_PHASES builds; else 0)
+int peps_phase_read_f64(unsigned long long* out, int n);
+int peps_phase_read_ff(unsigned long long* out, int n);
+int peps_phase_read_f32(unsigned long long* out, int n);
 cudaError_t peps_launch_reduce(const double* psum, int nslots, int64_t len, double* sd,
                                double* sde, double* se, int accumulate, cudaStream_t st);
 cudaError_t peps_launch_convert(int precision, const double* A, void* As, int64_t n, int* flags,

@@ -89,6 +89,7 @@ __device__ double compress_row(const PepsPlan& P, const PepsStep& st, bool above
   const int sP = above ? D : 1, sQ = above ? 1 : D;  // strides of p, q in T
   const int64_t SC = P.site_cap, MC = P.mat_cap;
   double logs = log_in;
+  PEPS_TIC(t_comp);
   // R_{-1} = [1]
   if (threadIdx.x == 0) w.rst[0] = Arith<R>::one();
   __syncthreads();
@@ -121,7 +122,9 @@ __device__ double compress_row(const PepsPlan& P, const PepsStep& st, bool above
     c.k1 = Dl; c.ka1 = p * b; c.kb1 = D3;
     c.k2 = p; c.ka2 = b; c.kb2 = sP;
     contract<R>(c, w.b0, T, w.b1);
+    PEPS_TIC(t_qr);
     householder_r<R>(w.b1, mrow, Bj, w.rst + (int64_t)(j + 1) * MC, w.wsh, w.qrv);
+    PEPS_TOC(t_qr, PH_QR);
     rprev = st.r[j];
     // only the row space of R_j matters: keep it at unit scale so that the
     // float-float form stays inside the FP32 exponent range
@@ -180,10 +183,16 @@ __device__ double compress_row(const PepsPlan& P, const PepsStep& st, bool above
     normalize_pow2<R>(w.xj, rr * n, w.red);
     float* fsh = reinterpret_cast<float*>(w.rot);
     if (rr > n) {
+      PEPS_TIC(t_q2);
       householder_r<R>(w.xj, rr, n, w.b2, w.wsh, w.qrv);
+      PEPS_TOC(t_q2, PH_SVD_QR);
+      PEPS_TIC(t_svd);
       svd_topk_rows<R>(w.b2, n, n, kk, V, w.alpha, w.inv, fsh, w.wsh, w.red, w.qrv);
+      PEPS_TOC(t_svd, PH_SVD);
     } else {
+      PEPS_TIC(t_svd);
       svd_topk_rows<R>(w.xj, rr, n, kk, V, w.alpha, w.inv, fsh, w.wsh, w.red, w.qrv);
+      PEPS_TOC(t_svd, PH_SVD);
     }
     // C_j[(a,l)][k] = sum_{(q,c)} Y[(a,l)][(q,c)] V^T[k][(q,c)]
     c = ctr_init();
@@ -195,6 +204,7 @@ __device__ double compress_row(const PepsPlan& P, const PepsStep& st, bool above
     R* tmp = Cn; Cn = Cx; Cx = tmp;
     cn = kk;
   }
+  PEPS_TOC(t_comp, PH_COMPRESS);
   return logs;
 }
 

@@ -67,6 +67,7 @@ __device__ __forceinline__ int sweep_one(const PepsPlan& P, const PepsStep* step
     const R* Dn = w.dn + (int64_t)(i + 1) * P.env_cap;
     EnvDims Dd = env_dims(P, steps, (i + 1 <= L - 1) ? (L - 2 - i) : -1);
     // ---- horizontal moves on the one-row strip --------------------------
+    PEPS_TIC(t_h);
     strip1_right_all<R>(P, i, sp, As, U, Ud, Dn, Dd, w);
     if (threadIdx.x == 0) w.l1[0] = Arith<R>::one();
     __syncthreads();
@@ -109,11 +110,15 @@ __device__ __forceinline__ int sweep_one(const PepsPlan& P, const PepsStep* step
       }
       normalize_pow2<R>(out, env1_size(P, Ud, Dd, j + 1), w.red);
     }
+    PEPS_TOC(t_h, PH_SWEEP_1);
     if (i + 1 < L) {
       // ---- vertical moves on the two-row strip ---------------------------
       const R* Dn2 = w.dn + (int64_t)(i + 2) * P.env_cap;
       EnvDims Dd2 = env_dims(P, steps, (i + 2 <= L - 1) ? (L - 3 - i) : -1);
+      PEPS_TIC(t_r2);
       strip2_right_all<R>(P, i, sp, As, U, Ud, Dn2, Dd2, w);
+      PEPS_TOC(t_r2, PH_SWEEP_R2);
+      PEPS_TIC(t_v);
       if (threadIdx.x == 0) w.l2[0] = Arith<R>::one();
       __syncthreads();
       for (int j = 0; j < L; ++j) {
@@ -152,6 +157,7 @@ __device__ __forceinline__ int sweep_one(const PepsPlan& P, const PepsStep* step
         }
         normalize_pow2<R>(out, env2_size(P, Ud, Dd2, j + 1), w.red);
       }
+      PEPS_TOC(t_v, PH_SWEEP_2);
       // ---- absorb the updated row i into the upper environment -----------
       int unext = (ucur == 1) ? 2 : 1;
       compress_row<R>(P, steps[i], true, i, As, sp, U, 0.0,
@@ -226,10 +232,14 @@ __global__ void __launch_bounds__(PEPS_NT, PEPS_MINB) peps_vmc_kernel(EvalArgs<R
   for (int64_t c = blockIdx.x; c < a.B; c += gridDim.x) {
     const uint32_t chain = (uint32_t)(s.chain_offset + c);
     load_chain<R>(sh, s.state, c, N, chain, s.k0, s.k1);
+    PEPS_TIC(t_ev);
     evaluate_one<R>(a, c, sh, w, ps, false);
+    PEPS_TOC(t_ev, PH_EVAL);
     const uint32_t sw = s.sweep_dev ? *s.sweep_dev : (uint32_t)s.first_sweep;
+    PEPS_TIC(t_sw);
     const int acc = sweep_one<R>(P, a.steps, a.As, s.k0, s.k1, chain, sw,
                                  sh, w, true);
+    PEPS_TOC(t_sw, PH_SWEEP);
     for (int m = threadIdx.x; m < N; m += blockDim.x) s.state[c * N + m] = sh.sp[m];
     if (threadIdx.x == 0 && s.accepted) s.accepted[c] = acc;
     __syncthreads();
