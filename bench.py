@@ -46,11 +46,22 @@ E2E_MAX_STEPS = 3
 # same kernel, scaled by the chains it processed; the summaries under
 # profiles/ give the command).  Keyed by (workload, precision form); only
 # valid for the kernel the capture was taken from.
+# DRAM bytes per chain of the fused kernel, from one ncu capture of a 32-chain
+# launch, keyed by (workload, form, library variant): a kernel that has
+# changed since its capture has no entry, and its line reports null
 TRAFFIC_PER_CHAIN = {
-    # 32-chain launch of the tuned variant: 8.162 GB read + 44.148 GB written
-    # (profiles/peps_vmc_16x16_D6_Dc24_mixed_traffic.md)
-    ("16x16_D6_Dc24", "mixed"): (8162261504 + 44147782144) / 32,
+    # 8.162 GB read + 44.148 GB written (profiles/peps_vmc_16x16_D6_Dc24_mixed_traffic.md,
+    # the variant with the QR column prefetch and A'^T v one thread per column)
+    ("16x16_D6_Dc24", "mixed", "mixed-PEPS_BIDIAG_TPC1-PEPS_CTR_PIPE0-PEPS_QR_ACC0-PEPS_QR_PREFETCH1"):
+        (8162261504 + 44147782144) / 32,
 }
+
+
+def library_tag(ctx):
+    """The variant tag of the library a context runs on ('default' for the
+    default build)."""
+    d = os.path.basename(os.path.dirname(getattr(ctx.lib, "_name", "") or ""))
+    return "default" if d in ("", "lib") else d
 METRIC = "local-energy samples/s at 16x16 D=6 Dc=24, mixed vs FP64; p50/p99 latency"
 
 
@@ -531,6 +542,7 @@ def main():
     ctx = P.PepsContext(L, D, Dc, precision=args.precision, slots=args.slots)
     ctx.set_tensors(A)
     slots = ctx.slots
+    variant = library_tag(ctx)
     full_batch = cfg.get("batch", cfg.get("chains", 256))
     B = args.batch or 2 * slots
     seed = 0x5EED0000 + cfg["seed"]
@@ -675,8 +687,9 @@ def main():
     else:
         peak, unit = sms * 128 * 2 * sm_max * 1e6 / 1e12, "TFLOP/s (FP32 pipe)"
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": unit,
-            "frac": achieved / peak, "traffic": (TRAFFIC_PER_CHAIN[(args.workload, args.precision)] * B
-                        if (args.workload, args.precision) in TRAFFIC_PER_CHAIN else None),
+            "frac": achieved / peak,
+            "traffic": (TRAFFIC_PER_CHAIN[(args.workload, args.precision, variant)] * B
+                        if (args.workload, args.precision, variant) in TRAFFIC_PER_CHAIN else None),
             "kernel": "peps_vmc_kernel",
             "flops_per_sample": flops,
             "flops_source": "oracle operation counter (1 chain)" if oflops else "kernel model",
@@ -698,7 +711,8 @@ def main():
                        "recipe": cfg["recipe"], "precision": args.precision,
                        "step": "fused evaluate (E, ratios, Delta sums) + 1 Metropolis sweep, slot "
                                "reduction, GO update",
-                       "l2": "per-chain working sets (%d slots) exceed L2 (129 MB)" % slots},
+                       "l2": "per-chain working sets (%d slots) exceed L2 (129 MB)" % slots,
+                       "library": variant},
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "latency_per": "batch (one step)",
             "roofline": roof, "cpu_baseline": cpu,

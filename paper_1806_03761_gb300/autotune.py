@@ -32,7 +32,7 @@ import time
 from . import build as B
 
 CANDIDATES = [
-    {},                                   # the default
+    {},                                   # the default (pipelined contractions, compensated QR update)
     {"PEPS_QR_PREFETCH": 1},
     {"PEPS_BIDIAG_TPC": 1},
     {"PEPS_QR_PREFETCH": 1, "PEPS_BIDIAG_TPC": 1},
@@ -42,15 +42,12 @@ CANDIDATES = [
     {"PEPS_BA_FF": 2, "PEPS_BA_F64": 1},
     {"PEPS_MINB": 1, "PEPS_NT": 512},     # one block of 16 warps per SM
     {"PEPS_MINB": 1},                     # one block of 8 warps per SM, 255 registers
-    {"PEPS_QR_PREFETCH": 1, "PEPS_BIDIAG_TPC": 1, "PEPS_CTR_PIPE": 1},
-    {"PEPS_QR_PREFETCH": 1, "PEPS_BIDIAG_TPC": 1, "PEPS_QR_ACC": 1},
-    {"PEPS_QR_PREFETCH": 1, "PEPS_BIDIAG_TPC": 1, "PEPS_CTR_PIPE": 1, "PEPS_QR_ACC": 1},
-    {"PEPS_QR_PREFETCH": 1, "PEPS_BIDIAG_TPC": 1, "PEPS_CTR_PIPE": 1, "PEPS_QR_ACC": 1,
-     "PEPS_BB_FF": 4},
-    {"PEPS_QR_PREFETCH": 1, "PEPS_BIDIAG_TPC": 1, "PEPS_QR_TALL_PAIR": 1, "PEPS_CTR_PIPE": 1,
-     "PEPS_QR_ACC": 1},
-    {"PEPS_QR_PREFETCH": 1, "PEPS_BIDIAG_TPC": 1, "PEPS_CTR_PIPE": 1, "PEPS_QR_ACC": 1,
-     "PEPS_MINB": 3},                     # three blocks of 8 warps per SM, 80 registers
+    {"PEPS_QR_PREFETCH": 1, "PEPS_BIDIAG_TPC": 1, "PEPS_CTR_PIPE": 0, "PEPS_QR_ACC": 0},
+    {"PEPS_QR_PREFETCH": 1, "PEPS_BIDIAG_TPC": 1, "PEPS_BB_FF": 4},
+    {"PEPS_QR_PREFETCH": 1, "PEPS_BIDIAG_TPC": 1, "PEPS_MINB": 3},  # 3 blocks per SM, 80 registers
+    {"PEPS_QR_PREFETCH": 1, "PEPS_BIDIAG_TPC": 1, "PEPS_QR_TALL_PAIR": 1, "PEPS_MINB": 3},
+    {"PEPS_QR_PREFETCH": 1, "PEPS_BIDIAG_TPC": 1, "PEPS_MINB": 3, "PEPS_BA_FF": 2},
+    {"PEPS_QR_PREFETCH": 1, "PEPS_BIDIAG_TPC": 1, "PEPS_MINB": 4},  # 4 blocks per SM, 64 registers
 ]
 
 

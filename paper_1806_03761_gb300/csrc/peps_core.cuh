@@ -108,11 +108,12 @@ __device__ __forceinline__ Ctr ctr_init() {
 #ifndef PEPS_BB_FF
 #define PEPS_BB_FF 2
 #endif
-// PEPS_CTR_PIPE=1: the operands of reduction step t + 1 are loaded before
-// the multiply-adds of step t, so that their latency overlaps the arithmetic
-// (the same products summed in the same order: bit-identical results).
+// PEPS_CTR_PIPE=1 (default): the operands of reduction step t + 1 are loaded
+// before the multiply-adds of step t, so that their latency overlaps the
+// arithmetic (the same products summed in the same order: bit-identical to
+// PEPS_CTR_PIPE=0).
 #ifndef PEPS_CTR_PIPE
-#define PEPS_CTR_PIPE 0
+#define PEPS_CTR_PIPE 1
 #endif
 template <class R> struct ContractBlock {
   static constexpr int BA = PEPS_BA_FF, BB = PEPS_BB_FF;
@@ -419,12 +420,13 @@ __device__ void householder_r_unblocked(R* X, int m, int n, R* Rout, R* sh) {
 #endif
 #define PEPS_QR_ROWS 896
 
-// PEPS_QR_ACC=1: the trailing update's warp reductions merge the lanes'
-// compensated accumulators directly, and x - V w' is one compensated
+// PEPS_QR_ACC=1 (default): the trailing update's warp reductions merge the
+// lanes' compensated accumulators directly, and x - V w' is one compensated
 // accumulation per element (float-float: fewer FP32 operations at the same
-// error bound, a few 2^-48 of |x| + |V w'|; FP64: bit-identical).
+// error bound, a few 2^-48 of |x| + |V w'|; FP64 and FP32: bit-identical to
+// PEPS_QR_ACC=0).
 #ifndef PEPS_QR_ACC
-#define PEPS_QR_ACC 0
+#define PEPS_QR_ACC 1
 #endif
 
 // Apply the panel's reflectors (explicit vectors v_s, zero above row s and

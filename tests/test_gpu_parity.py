@@ -370,20 +370,20 @@ def _vmc_outputs(ctx, A, spins):
     ("mixed", {"PEPS_QR_PREFETCH": 1, "PEPS_BIDIAG_TPC": 1}),
 ])
 def test_pipelined_contraction_is_bit_identical(prec, base):
-    """PEPS_CTR_PIPE loads the next reduction step's operands ahead of the
-    multiply-adds: every product and sum is the same, so the fused step's
-    outputs equal those of the build without it bit for bit (8x8, D=4,
-    Dc=16: every contraction shape of the strips and the absorption; FP64
-    also with PEPS_QR_ACC, the same fused multiply-adds in FP64)."""
+    """PEPS_CTR_PIPE (the default) loads the next reduction step's operands
+    ahead of the multiply-adds: every product and sum is the same, so the
+    fused step's outputs equal those of a build without it bit for bit (8x8,
+    D=4, Dc=16: every contraction shape of the strips and the absorption;
+    FP64 also without PEPS_QR_ACC, the same fused multiply-adds in FP64)."""
     from paper_1806_03761_gb300 import PepsContext
     L, D, Dc = 8, 4, 16
     A = make_peps(L, D, seed=81)
     spins = random_sz0_configs(L, 6, seed=82)
-    ref = _vmc_outputs(PepsContext(L, D, Dc, precision=prec, slots=3, variant=base or None), A, spins)
-    knobs = dict(base, PEPS_CTR_PIPE=1)
+    got = _vmc_outputs(PepsContext(L, D, Dc, precision=prec, slots=3, variant=base or None), A, spins)
+    knobs = dict(base, PEPS_CTR_PIPE=0)
     if prec == "fp64":
-        knobs["PEPS_QR_ACC"] = 1
-    got = _vmc_outputs(PepsContext(L, D, Dc, precision=prec, slots=3, variant=knobs), A, spins)
+        knobs["PEPS_QR_ACC"] = 0
+    ref = _vmc_outputs(PepsContext(L, D, Dc, precision=prec, slots=3, variant=knobs), A, spins)
     assert set(ref) == set(got)
     for k in ref:
         assert np.array_equal(ref[k], got[k]), k
