@@ -50,8 +50,13 @@ E2E_MAX_STEPS = 3
 # launch, keyed by (workload, form, library variant): a kernel that has
 # changed since its capture has no entry, and its line reports null
 TRAFFIC_PER_CHAIN = {
-    # 8.162 GB read + 44.148 GB written (profiles/peps_vmc_16x16_D6_Dc24_mixed_traffic.md,
-    # the variant with the QR column prefetch and A'^T v one thread per column)
+    # 8.375 GB read + 46.217 GB written (profiles/peps_vmc_16x16_D6_Dc24_mixed_traffic.md:
+    # the tuned variant, three blocks per SM, QR column prefetch, A'^T v one
+    # thread per column, pipelined contractions, compensated QR update)
+    ("16x16_D6_Dc24", "mixed", "mixed-PEPS_BIDIAG_TPC1-PEPS_MINB3-PEPS_QR_PREFETCH1"):
+        (8375110144 + 46216911872) / 32,
+    # the earlier variant (two blocks per SM, neither of the last two paths):
+    # 8.162 GB read + 44.148 GB written
     ("16x16_D6_Dc24", "mixed", "mixed-PEPS_BIDIAG_TPC1-PEPS_CTR_PIPE0-PEPS_QR_ACC0-PEPS_QR_PREFETCH1"):
         (8162261504 + 44147782144) / 32,
 }
@@ -79,9 +84,10 @@ def parse():
     p.add_argument("--dt", type=float, default=1e-3)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--mode", default="vmc",
-                   choices=["vmc", "serving", "contraction", "correlations", "multi"],
+                   choices=["vmc", "serving", "contraction", "correlations", "multi", "phases"],
                    help="serving: a Poisson stream of evaluation jobs through peps_server_*; "
-                        "contraction: tensor-core vs CUDA-core column-step contractions")
+                        "contraction: tensor-core vs CUDA-core column-step contractions; "
+                        "phases: per-phase cycles of the fused VMC kernel")
     p.add_argument("--arrival-s", type=float, default=20.0,
                    help="serving: length of the arrival window per precision form")
     p.add_argument("--rates", default="0.25,0.5,1.0",
@@ -510,8 +516,50 @@ def run_multi(args):
                       "results": res}), flush=True)
 
 
+def run_phases(args):
+    """--mode phases: per-phase clock64 cycles of the fused VMC kernel, from a
+    PEPS_PHASES build of the library variant the tuning table names for the
+    workload's shape (the same kernel otherwise): one wave of chains, one
+    uncounted step, then one counted step; cycles per chain and shares of
+    evaluation + sweep.  Not a throughput measurement."""
+    import torch
+
+    import paper_1806_03761_gb300 as P
+    from paper_1806_03761_gb300 import build as B
+    from synth import make_peps
+    cfg = dict(CONFIGS[args.workload])
+    L, D, Dc = cfg["L"], cfg["D"], cfg["Dc"]
+    entry = json.load(open(B.TUNING)).get(P.tuning_key(L, D, Dc, args.precision)) \
+        if os.path.exists(B.TUNING) else None
+    knobs = dict(entry["choice"]) if entry else {}
+    knobs["PEPS_PHASES"] = 1
+    A = torch.from_numpy(make_peps(L, D, cfg["seed"], cfg["recipe"], cfg.get("eps", 1e-2))).cuda()
+    ctx = P.PepsContext(L, D, Dc, precision=args.precision, variant=knobs)
+    ctx.set_tensors(A)
+    n = ctx.slots
+    state = ctx.sample(0x5EED0000 + cfg["seed"], n, 0, 1, 1).contiguous()
+    ctx.vmc_step(0x5EED0000 + cfg["seed"], state, 1)
+    torch.cuda.synchronize()
+    ctx.phase_cycles()
+    ctx.vmc_step(0x5EED0000 + cfg["seed"], state, 2)
+    torch.cuda.synchronize()
+    ph = ctx.phase_cycles()
+    rc, flags = ctx.sync_status()
+    total = ph["eval"] + ph["sweep"]
+    print(json.dumps({"metric": "fused VMC kernel cycles per chain by phase (clock64, one block)",
+                      "workload": args.workload, "precision": args.precision, "chains": n,
+                      "library": B.variant_tag(dict(B.DEFAULTS, **knobs), args.precision),
+                      "mcycles_per_chain": {k: v / n / 1e6 for k, v in ph.items()},
+                      "share_of_step": {k: v / total for k, v in ph.items()},
+                      "status": {"rc": rc, "flags": flags}}), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
+    if args.mode == "phases":
+        run_phases(args)
+        return
     if args.mode == "multi":
         run_multi(args)
         return

@@ -429,3 +429,34 @@ def test_compensated_tall_pair_update_matches_the_oracle():
     assert np.max(np.abs(r["log_abs"] - ref["log_abs"])) <= TOL["mixed"]
     assert np.max(np.abs(r["e_loc"] - ref["e_loc"]) /
                   np.maximum(1.0, np.abs(ref["e_loc"]))) <= TOL["mixed"]
+
+
+def test_tuned_variants_match_the_oracle():
+    """Every library variant the tuning table selects (the code paths and
+    launch shape a shape's contexts run on) evaluates the chains'
+    configurations as the oracle does: 6x6 D=8 Dc=32 (2048 x 256 QR panels)
+    for a variant with the two-warp tall panels, else 6x6 D=6 Dc=24
+    (864 x 144 panels, the 16x16 workload's site shapes)."""
+    import json
+    from paper_1806_03761_gb300 import PepsContext
+    from paper_1806_03761_gb300 import build as B
+    table = json.load(open(B.TUNING))
+    seen = set()
+    for key, entry in sorted(table.items()):
+        prec, knobs = entry["precision"], entry["choice"]
+        tag = B.variant_tag(dict(B.DEFAULTS, **knobs), prec)
+        if tag in seen:
+            continue
+        seen.add(tag)
+        L, D, Dc = (6, 8, 32) if knobs.get("PEPS_QR_TALL_PAIR") else (6, 6, 24)
+        A = make_peps(L, D, seed=95)
+        spins = random_sz0_configs(L, 2, seed=96)
+        c = PepsContext(L, D, Dc, precision=prec, slots=2, variant=knobs)
+        r = _vmc_outputs(c, A, spins)
+        c.close()
+        ref = oracle.evaluate_batch(A, spins, L, Dc)
+        assert np.array_equal(r["sign"], ref["sign"].astype(np.int8)), tag
+        assert np.max(np.abs(r["log_abs"] - ref["log_abs"])) <= TOL[prec], tag
+        assert np.max(np.abs(r["e_loc"] - ref["e_loc"]) /
+                      np.maximum(1.0, np.abs(ref["e_loc"]))) <= TOL[prec], tag
+    assert seen
