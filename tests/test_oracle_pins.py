@@ -200,6 +200,49 @@ def test_compress_keeps_chi_largest_singular_values():
     assert np.allclose(got, best, atol=1e-12 * S[0])
 
 
+def _tt_svd_right_to_left(psi, chi):
+    """Sequential truncated SVDs of a full tensor from its last index to its
+    first (the tensor-train SVD of Oseledets, 2011, run right to left),
+    keeping chi singular values at every bond; returns the truncated
+    tensor.  Written on the full vector, independent of any MPS."""
+    dims = psi.shape
+    L = len(dims)
+    cur = psi.reshape(-1, dims[-1])
+    right = np.eye(dims[-1]).reshape(dims[-1], dims[-1])  # rows: kept basis of the right part
+    for j in range(L - 1, 0, -1):
+        U, S, Vt = np.linalg.svd(cur, full_matrices=False)
+        k = min(chi, S.size)
+        right = Vt[:k] @ right                       # k x (p_j ... p_{L-1})
+        right = right.reshape(k, -1)
+        cur = (U[:, :k] * S[:k]).reshape(-1, dims[j - 1] * k)
+        right = np.kron(np.eye(dims[j - 1]), right).reshape(dims[j - 1] * k, -1)
+    return (cur @ right).reshape(dims)
+
+
+def test_compress_is_the_sequential_truncated_svd_of_the_state():
+    """A truncated five-site MPS (bonds up to 9, chi = 3) represents the
+    tensor that sequential truncated SVDs of the exact state vector give,
+    bond by bond from the right (numpy SVD of the full 3^5 tensor): the QR
+    sweep makes the left part an isometry, so every SVD of the sweep sees
+    the full reshaped state."""
+    rng = np.random.default_rng(11)
+    bonds = [1, 3, 9, 9, 3, 1]
+    sites = [rng.standard_normal((bonds[j], 3, bonds[j + 1])) for j in range(5)]
+    psi = sites[0]
+    for M in sites[1:]:
+        psi = np.tensordot(psi, M, axes=([-1], [0]))
+    psi = psi.reshape((3,) * 5)
+    want = _tt_svd_right_to_left(psi, 3)
+    out = op.compress(op.BMPS([x.copy() for x in sites]), 3)
+    got = out.sites[0]
+    for M in out.sites[1:]:
+        got = np.tensordot(got, M, axes=([-1], [0]))
+    got = got.reshape((3,) * 5) * np.exp(out.logscale)
+    assert max(M.shape[2] for M in out.sites) == 3
+    assert np.linalg.norm(psi - want) > 1e-3 * np.linalg.norm(psi)  # truncation is active
+    assert np.allclose(got, want, atol=1e-11 * np.abs(want).max())
+
+
 # --------------------------------------------------------------------------
 # Log-derivatives (Eq. delta) and the gradient (Eq. gradients)
 # --------------------------------------------------------------------------
