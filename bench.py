@@ -38,7 +38,7 @@ sys.path.insert(0, ROOT)
 from synth import CONFIGS, make_peps  # noqa: E402
 
 WORKLOAD = "16x16_D6_Dc24"
-FP64_MAX_WARMUP, FP64_MAX_STEPS = 2, 5
+FP64_MAX_WARMUP, FP64_MAX_STEPS = 1, 3
 E2E_MAX_STEPS = 3
 
 # DRAM traffic of one launch of the fused kernel, bytes per chain (ncu
