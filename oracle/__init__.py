@@ -12,9 +12,12 @@ silent the reading taken is stated in the function's docstring.
 
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
 against brute-force contraction, exact diagonalisation, closed forms, finite
-differences, published Philox known-answer vectors or exact invariants, except
-that the truncated regime (D_c below the exact bond dimension) is pinned only
-through its exact special cases and invariants ("parity by same algorithm").
+differences, published Philox known-answer vectors or exact invariants.  In
+the truncated regime (D_c below the exact bond dimension) the compression is
+pinned against sequential truncated SVDs of the exact state vector (the
+tensor-train SVD), and the evaluation on truncated environments through
+invariants that hold at any D_c (the strip-local ratio and log-derivative
+definitions, sum_T T Delta = 1 per site).
 """
 from .peps import (  # noqa: F401
     bond_list, site_tensor, BMPS, compress, upper_envs, lower_envs,
