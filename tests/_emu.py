@@ -1,0 +1,112 @@
+"""Build the library's kernels and C ABI for the host (tests/host/emu): every
+kernel launch `k<<<grid, block, ...>>>(args)` of the CUDA translation units
+is rewritten to `emu_launch(grid, block, [=] { k(args); })`, and the units
+are compiled with g++ against the emulated runtime header.  Only tests use
+it; the product is the CUDA build."""
+import concurrent.futures as cf
+import os
+import re
+import shutil
+import subprocess
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(ROOT, "paper_1806_03761_gb300", "csrc")
+EMU = os.path.join(HERE, "host", "emu")
+# the units without tensor-core, static-scratch or server code
+UNITS = ["peps_api.cu", "peps_k_misc.cu"] + [
+    "peps_k_%s_%s.cu" % (k, f) for k in ("eval", "sample", "vmc") for f in ("f64", "ff", "f32")] + [
+    "peps_k_%s_%s.cu" % (k, f) for k in ("corr", "multi") for f in ("f64", "ff")]
+
+_LAUNCH = re.compile(r"(\b[A-Za-z_]\w*(?:<[^<>;]*>)?)\s*<<<([^>]*)>>>\s*\((.*?)\)\s*;", re.S)
+
+
+def rewrite(src):
+    def sub(m):
+        cfg = [x.strip() for x in m.group(2).split(",")]
+        return "emu_launch(dim3(%s), dim3(%s), [=]() { %s(%s); });" % (cfg[0], cfg[1], m.group(1),
+                                                                   m.group(3))
+    return _LAUNCH.sub(sub, src)
+
+
+def build(outdir, defines=(), sanitize=False):
+    """Compile and link the emulated library into outdir; returns its path.
+    sanitize: instrument it with AddressSanitizer (the process that loads it
+    needs libasan preloaded)."""
+    gxx = shutil.which("g++")
+    if not gxx:
+        raise RuntimeError("no g++")
+    os.makedirs(outdir, exist_ok=True)
+    opt = ["-O1", "-g", "-fsanitize=address", "-fno-omit-frame-pointer"] if sanitize else ["-O2"]
+    flags = [gxx, "-std=c++20", "-ffp-contract=off", "-fPIC", "-pthread", "-w",
+             "-I", EMU, "-I", CSRC, "-I", os.path.join(ROOT, "include")] + opt + \
+        ["-D%s" % d for d in defines]
+    jobs = []
+    for u in UNITS:
+        dst = os.path.join(outdir, u[:-3] + ".cpp")
+        with open(os.path.join(CSRC, u)) as f:
+            text = rewrite(f.read())
+        with open(dst, "w") as f:
+            f.write('#include "cuda_runtime.h"\n' + text)
+        jobs.append((dst, dst[:-4] + ".o"))
+    jobs.append((os.path.join(EMU, "emu.cpp"), os.path.join(outdir, "emu.o")))
+
+    def cc(j):
+        r = subprocess.run(flags + ["-c", j[0], "-o", j[1]], capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("g++ failed on %s:\n%s" % (j[0], r.stderr[-4000:]))
+        return j[1]
+    with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
+        objs = list(ex.map(cc, jobs))
+    lib = os.path.join(outdir, "libpeps_emu.so")
+    r = subprocess.run([gxx, "-shared", "-pthread"] + (["-fsanitize=address"] if sanitize else []) +
+                       ["-o", lib] + objs, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("link failed:\n" + r.stderr[-4000:])
+    return lib
+
+
+def _asan_cases(lib_path):
+    """Evaluation, sampling and the fused step of both forms at 4x4, D=3,
+    Dc=4 on the instrumented library (run in a process with libasan
+    preloaded); prints each case's energy error against the oracle."""
+    import ctypes
+    import sys
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import oracle
+    from paper_1806_03761_gb300 import _lib as B
+    from synth import make_peps, random_sz0_configs
+    from tests.test_emu_parity import Ctx
+    lib = ctypes.CDLL(lib_path)
+    for name, (res, args) in B._SIGS.items():
+        if hasattr(lib, name):
+            fn = getattr(lib, name)
+            fn.restype, fn.argtypes = res, args
+    for prec in ("fp64", "mixed"):
+        c = Ctx(lib, 4, 3, 4, prec, slots=2)
+        A = make_peps(4, 3, seed=7)
+        c.set_tensors(A)
+        sp = random_sz0_configs(4, 2, seed=8)
+        r = c.evaluate(sp)
+        st, _ = c.sample(99, 2, 1, 1, 1)
+        c.vmc_step(99, st.copy(), 3)
+        ref = oracle.evaluate_batch(A, sp, 4, 4)
+        print(prec, "status", c.status(), "energy error %.2e" % np.max(np.abs(r["e_loc"] - ref["e_loc"])),
+              flush=True)
+        c.close()
+
+
+if __name__ == "__main__":
+    # python -m tests._emu --asan-check: the emulated kernels under
+    # AddressSanitizer (any out-of-bounds access of a buffer aborts the run)
+    import sys
+    import tempfile
+    if sys.argv[1:2] == ["--asan-check"]:
+        path = build(tempfile.mkdtemp(prefix="emu_asan"), sanitize=True)
+        libasan = subprocess.run(["gcc", "-print-file-name=libasan.so"], capture_output=True,
+                                 text=True).stdout.strip()
+        env = dict(os.environ, LD_PRELOAD=libasan, ASAN_OPTIONS="detect_leaks=0")
+        r = subprocess.run([sys.executable, "-c", "from tests._emu import _asan_cases; _asan_cases(%r)" % path],
+                           cwd=ROOT, env=env)
+        sys.exit(r.returncode)

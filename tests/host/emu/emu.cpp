@@ -1,0 +1,96 @@
+// Launch machinery of the host emulation (see cuda_runtime.h): the threads
+// of a block are ucontext fibers of the calling host thread.
+#include <ucontext.h>
+
+#include <cstdio>
+#include <vector>
+
+#include "cuda_runtime.h"
+
+uint3 threadIdx;
+uint3 blockIdx;
+dim3 blockDim;
+dim3 gridDim;
+EmuBarrier emu_block_bar;
+EmuBarrier emu_warp_bar[32];
+uint64_t emu_slot[32][32];
+int emu_acc;
+
+namespace {
+struct Fiber {
+  ucontext_t ctx;
+  const long* wait_on;  // generation counter this fiber waits to change
+  long wait_gen;
+  bool done;
+};
+ucontext_t g_sched;
+std::vector<Fiber> g_fibers;
+int g_cur;
+const std::function<void()>* g_body;
+constexpr size_t kStack = 256 * 1024;
+
+void fiber_entry() {
+  (*g_body)();
+  g_fibers[g_cur].done = true;
+  swapcontext(&g_fibers[g_cur].ctx, &g_sched);
+}
+}  // namespace
+
+void emu_wait(EmuBarrier& b) {
+  const long g = b.gen;
+  if (++b.count == b.n) {
+    b.count = 0;
+    ++b.gen;
+    return;
+  }
+  Fiber& f = g_fibers[g_cur];
+  f.wait_on = &b.gen;
+  f.wait_gen = g;
+  swapcontext(&f.ctx, &g_sched);
+}
+
+void emu_launch(dim3 grid, dim3 block, const std::function<void()>& body) {
+  const unsigned nt = block.x, nb = grid.x;
+  if (nt == 0 || nb == 0) return;
+  std::vector<std::vector<char>> stacks(nt, std::vector<char>(kStack));
+  g_fibers.assign(nt, Fiber{});
+  g_body = &body;
+  blockDim = block;
+  gridDim = grid;
+  for (unsigned x = 0; x < nb; ++x) {
+    blockIdx = uint3{x, 0, 0};
+    emu_block_bar = EmuBarrier{0, 0, (int)nt};
+    for (unsigned w = 0; w < 32; ++w) {
+      const int n = (w + 1) * 32 <= nt ? 32 : (w * 32 < nt ? (int)(nt - w * 32) : 0);
+      emu_warp_bar[w] = EmuBarrier{0, 0, n};
+    }
+    for (unsigned t = 0; t < nt; ++t) {
+      Fiber& f = g_fibers[t];
+      f = Fiber{};
+      getcontext(&f.ctx);
+      f.ctx.uc_stack.ss_sp = stacks[t].data();
+      f.ctx.uc_stack.ss_size = kStack;
+      f.ctx.uc_link = nullptr;
+      makecontext(&f.ctx, fiber_entry, 0);
+    }
+    unsigned alive = nt;
+    while (alive > 0) {
+      bool progress = false;
+      for (unsigned t = 0; t < nt; ++t) {
+        Fiber& f = g_fibers[t];
+        if (f.done || (f.wait_on && *f.wait_on == f.wait_gen)) continue;
+        f.wait_on = nullptr;
+        g_cur = (int)t;
+        threadIdx = uint3{t, 0, 0};
+        swapcontext(&g_sched, &f.ctx);
+        progress = true;
+        if (f.done) --alive;
+      }
+      if (!progress) {
+        std::fprintf(stderr, "emulation: block %u deadlocked (%u threads parked at a barrier)\n", x,
+                     alive);
+        std::abort();
+      }
+    }
+  }
+}

@@ -1,0 +1,196 @@
+"""The library's kernels and C ABI built for the host (tests/_emu.py: the
+CUDA translation units compiled with g++ against an emulated runtime, the
+threads of a block run as fibers) against the oracle on small lattices: the
+evaluation (E, log|W|, sign, every ratio, flip counts, Delta sums) in both
+forms, the fused VMC step against evaluation then sweep, and bit-exact
+Metropolis chains and GO update.  The kernel source is the GPU build's;
+these tests check its logic without a GPU (FP32 operations are IEEE, with
+no fused multiply-add contraction, so roundings may differ from the GPU's
+at the last bit)."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import make_peps, random_sz0_configs
+
+from . import _emu
+
+TOL = {"fp64": 1e-10, "mixed": 1e-4}
+
+
+@pytest.fixture(scope="module")
+def lib(tmp_path_factory):
+    from paper_1806_03761_gb300 import _lib as B
+    try:
+        path = _emu.build(str(tmp_path_factory.mktemp("emu")))
+    except RuntimeError as e:
+        pytest.skip(str(e))
+    L = ctypes.CDLL(path)
+    for name, (res, args) in B._SIGS.items():
+        if hasattr(L, name):
+            fn = getattr(L, name)
+            fn.restype, fn.argtypes = res, args
+    return L
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Ctx:
+    """A context of the emulated library; numpy arrays stand for device
+    buffers (the emulated device memory is host memory)."""
+
+    def __init__(self, lib, L, D, Dc, prec, slots=0):
+        from paper_1806_03761_gb300 import _lib as B
+        self.lib, self.L, self.D, self.N = lib, L, D, L * L
+        self.nb = 2 * L * (L - 1) + 2 * (L - 1) ** 2
+        code = {"fp64": B.PEPS_FP64, "mixed": B.PEPS_MIXED}[prec]
+        self.shape = B.PepsShape(L, D, Dc, 1.0, 0.5, code)
+        self.h = ctypes.c_void_p()
+        assert lib.peps_create(ctypes.byref(self.shape), slots, ctypes.byref(self.h)) == 0
+
+    def set_tensors(self, A):
+        self.A = np.ascontiguousarray(A)
+        assert self.lib.peps_set_tensors(self.h, _p(self.A), None) == 0
+
+    def status(self):
+        f = ctypes.c_int32(0)
+        rc = self.lib.peps_sync_status(self.h, None, ctypes.byref(f))
+        return rc, f.value
+
+    def sums(self):
+        n = self.N * 2 * self.D ** 4
+        return np.zeros(n), np.zeros(n), np.zeros(1)
+
+    def evaluate(self, spins):
+        B = len(spins)
+        sp = np.ascontiguousarray(spins, np.uint8)
+        r = dict(e_loc=np.zeros(B), log_abs=np.zeros(B), sign=np.zeros(B, np.int8),
+                 ratios=np.zeros((B, self.nb)), n_flips=np.zeros(B, np.int32))
+        sd, sde, se = self.sums()
+        assert self.lib.peps_evaluate(self.h, _p(sp), B, _p(r["e_loc"]), _p(r["log_abs"]),
+                                      _p(r["sign"]), _p(r["ratios"]), _p(r["n_flips"]), None,
+                                      _p(sd), _p(sde), _p(se), 0, None) == 0
+        r.update(sum_delta=sd, sum_delta_e=sde, sum_e=se)
+        return r
+
+    def vmc_step(self, seed, state, sweep):
+        B = len(state)
+        assert state.shape == (B, self.N) and state.dtype == np.uint8
+        r = dict(e_loc=np.zeros(B), log_abs=np.zeros(B), sign=np.zeros(B, np.int8),
+                 accepted=np.zeros(B, np.int64))
+        sd, sde, se = self.sums()
+        assert self.lib.peps_vmc_step(self.h, seed, B, 0, sweep, _p(state), _p(r["e_loc"]),
+                                      _p(r["log_abs"]), _p(r["sign"]), _p(sd), _p(sde), _p(se), 0,
+                                      _p(r["accepted"]), None) == 0
+        r.update(sum_delta=sd, sum_delta_e=sde, sum_e=se)
+        return r
+
+    def sample(self, seed, n, n_burn, n_thin, spc, first_sweep=1, state=None):
+        assert state is None or state.shape == (n, self.N)
+        out = np.zeros((n * spc, self.N), np.uint8)
+        acc = np.zeros(n, np.int64)
+        assert self.lib.peps_sample_batch(self.h, seed, n, 0, n_burn, n_thin, spc, first_sweep,
+                                          _p(out), _p(state), _p(acc), None) == 0
+        return out, acc
+
+    def close(self):
+        self.lib.peps_destroy(self.h)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("L,D,Dc", [(3, 2, 8), (4, 3, 4)])
+def test_evaluation_matches_the_oracle(lib, prec, L, D, Dc):
+    A = make_peps(L, D, seed=40 + L)
+    spins = random_sz0_configs(L, 3, seed=41 + L)
+    c = Ctx(lib, L, D, Dc, prec, slots=2)
+    c.set_tensors(A)
+    r = c.evaluate(spins)
+    assert c.status() == (0, 0)
+    c.close()
+    ref = oracle.evaluate_batch(A, spins, L, Dc, want_delta=True)
+    tol = TOL[prec]
+    assert np.array_equal(r["sign"], ref["sign"].astype(np.int8))
+    assert np.array_equal(r["n_flips"], ref["n_flips"])
+    assert np.max(np.abs(r["log_abs"] - ref["log_abs"])) <= tol
+    assert np.max(np.abs(r["e_loc"] - ref["e_loc"]) / np.maximum(1, np.abs(ref["e_loc"]))) <= tol
+    for b in range(len(spins)):
+        rr = ref["ratios"][b]
+        m = rr != 0
+        assert np.array_equal(r["ratios"][b] == 0, ~m)
+        floor = tol * np.sqrt(np.mean(rr[m] ** 2))
+        assert np.all(np.abs(r["ratios"][b][m] - rr[m]) <= tol * np.maximum(np.abs(rr[m]), floor / tol))
+    N, D4 = L * L, D ** 4
+    sd, sde = np.zeros((N, 2, D4)), np.zeros((N, 2, D4))
+    for b in range(len(spins)):
+        for m in range(N):
+            dv = ref["delta"][b, m, spins[b][m]].reshape(-1)
+            sd[m, spins[b][m]] += dv
+            sde[m, spins[b][m]] += dv * ref["e_loc"][b]
+    assert np.max(np.abs(r["sum_delta"].reshape(sd.shape) - sd)) <= tol * np.abs(sd).max()
+    assert np.max(np.abs(r["sum_delta_e"].reshape(sde.shape) - sde)) <= tol * np.abs(sde).max()
+    assert abs(r["sum_e"][0] - ref["e_loc"].sum()) <= tol * max(1, abs(ref["e_loc"].sum()))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_sampler_bit_exact(lib, prec):
+    """Metropolis chains (Fisher-Yates starts, exchange moves, Philox draws)
+    equal the oracle's configurations and acceptance counts bit for bit, and
+    resume from their final states."""
+    L, D, Dc = 4, 3, 4
+    A = make_peps(L, D, seed=1)
+    c = Ctx(lib, L, D, Dc, prec, slots=2)
+    c.set_tensors(A)
+    out, acc = c.sample(12345678901, 3, 1, 1, 1)
+    ref, fin, racc = oracle.sample_chains(A, L, Dc, 12345678901, 3, 1, 1, 1)
+    assert np.array_equal(out, ref) and np.array_equal(acc, racc)
+    assert racc.sum() > 0
+    state = fin.copy()
+    out2, _ = c.sample(12345678901, 3, 0, 1, 1, first_sweep=10, state=state)
+    ref2, fin2, _ = oracle.sample_chains(A, L, Dc, 12345678901, 3, 0, 1, 1, init=fin, first_sweep=10)
+    assert np.array_equal(out2, ref2) and np.array_equal(state, fin2)
+    assert c.status() == (0, 0)
+    c.close()
+
+
+def test_vmc_step_is_evaluation_then_sweep(lib):
+    """The fused step (evaluation, then one sweep reusing the lower
+    environments) equals peps_evaluate on the chains' states followed by one
+    sweep of peps_sample_batch, bit for bit."""
+    L, D, Dc = 4, 2, 4
+    A = make_peps(L, D, seed=51)
+    c = Ctx(lib, L, D, Dc, "fp64", slots=2)
+    c.set_tensors(A)
+    state0, _ = c.sample(77, 2, 1, 1, 1)
+    ev = c.evaluate(state0)
+    after = state0.copy()
+    c.sample(77, len(after), 0, 1, 1, first_sweep=5, state=after)
+    state = state0.copy()
+    r = c.vmc_step(77, state, 5)
+    for k in ("e_loc", "log_abs", "sign", "sum_delta", "sum_delta_e", "sum_e"):
+        assert np.array_equal(r[k], ev[k]), k
+    assert np.array_equal(state, after)
+    c.close()
+
+
+def test_grad_step_bit_exact(lib):
+    """The GO update (Eq. gradients, the sign step with Philox step lengths)
+    equals the oracle's, element by element."""
+    L, D = 4, 2
+    A = make_peps(L, D, seed=11)
+    rng = np.random.default_rng(12)
+    sd = rng.standard_normal((L * L, 2, D ** 4))
+    sde = rng.standard_normal((L * L, 2, D ** 4))
+    sd[0, 0, :3] = sde[0, 0, :3] = 0.0  # g = 0 exactly: unchanged
+    se = np.array([rng.standard_normal()])
+    M, dt, seed, step = 37, 0.05, 0xDEADBEEF12345, 9
+    c = Ctx(lib, L, D, 4, "fp64")
+    c.set_tensors(A)
+    Ad = A.copy()
+    assert lib.peps_grad_step(c.h, _p(sd), _p(sde), _p(se), M, dt, seed, step, _p(Ad), None) == 0
+    g = oracle.gradient(sd, sde, se[0], M)
+    assert np.array_equal(Ad, oracle.go_step(A, g.reshape(A.shape), dt, seed, step))
+    c.close()
