@@ -194,3 +194,64 @@ def test_grad_step_bit_exact(lib):
     g = oracle.gradient(sd, sde, se[0], M)
     assert np.array_equal(Ad, oracle.go_step(A, g.reshape(A.shape), dt, seed, step))
     c.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_correlations_match_the_oracle(lib, prec):
+    """The correlation kernel: S_a . S_m for every target, sources at the
+    centre and a corner, against the oracle's local estimator (the exchange
+    ratio relative, with a floor of tol * RMS of the sample's ratios)."""
+    from oracle import correlations as oc
+    L, D, Dc = 4, 3, 4
+    A = make_peps(L, D, seed=61)
+    spins = random_sz0_configs(L, 2, seed=62)
+    sources = np.array([oc.centre_site(L), 0], np.int32)
+    c = Ctx(lib, L, D, Dc, prec, slots=2)
+    c.set_tensors(A)
+    ss = np.zeros((2, len(sources), L * L))
+    mean = np.zeros((len(sources), L * L))
+    assert lib.peps_correlations(c.h, _p(np.ascontiguousarray(spins)), 2, len(sources), _p(sources),
+                                 _p(ss), _p(mean), None) == 0
+    assert c.status() == (0, 0)
+    c.close()
+    tol = TOL[prec]
+    for b, s in enumerate(spins):
+        for q, a in enumerate(sources):
+            ref = oc.local_correlations(A, s, L, Dc, int(a))
+            ex_ref, ex_got = ref - np.where(s == s[a], 0.25, -0.25), ss[b, q] - np.where(s == s[a], 0.25, -0.25)
+            ex_ref[a] = ex_got[a] = 0.0
+            floor = tol * max(np.sqrt(np.mean(ex_ref ** 2)), 1e-300)
+            assert np.all(np.abs(ex_got - ex_ref) <= np.maximum(tol * np.abs(ex_ref), floor)), (b, q)
+            assert ss[b, q, a] == 0.75
+    assert np.allclose(mean, ss.mean(axis=0), rtol=0, atol=1e-15)
+
+
+def test_multi_shape_launch_equals_each_context(lib):
+    """Jobs of three shapes in one persistent launch (the pool's work queue)
+    give each context's own local energies bit for bit."""
+    from paper_1806_03761_gb300 import _lib as B
+    shapes = [(3, 2, 4), (4, 2, 4), (4, 3, 4)]
+    ctxs, jobs, outs, refs, keep = [], [], [], [], []
+    arr = (B.PepsShape * len(shapes))()
+    for k, (L, D, Dc) in enumerate(shapes):
+        arr[k] = B.PepsShape(L, D, Dc, 1.0, 0.5, B.PEPS_MIXED)
+        c = Ctx(lib, L, D, Dc, "mixed", slots=2)
+        c.set_tensors(make_peps(L, D, seed=70 + k))
+        sp = np.ascontiguousarray(random_sz0_configs(L, 2, seed=80 + k))
+        refs.append(c.evaluate(sp)["e_loc"])
+        e = np.zeros(2)
+        keep.append(sp)
+        outs.append(e)
+        jobs.append(B.PepsMultiJob(c.h.value, _p(sp).value, 2, _p(e).value, None, None, None, None))
+        ctxs.append(c)
+    pool = ctypes.c_void_p()
+    assert lib.peps_pool_create(B.PEPS_MIXED, 3, arr, len(shapes), 8, ctypes.byref(pool)) == 0
+    jarr = (B.PepsMultiJob * len(jobs))(*jobs)
+    assert lib.peps_local_energy_multi(pool, jarr, len(jobs), None) == 0
+    f = ctypes.c_int32(0)
+    assert lib.peps_pool_sync_status(pool, None, ctypes.byref(f)) == 0 and f.value == 0
+    lib.peps_pool_destroy(pool)
+    for e, ref in zip(outs, refs):
+        assert np.array_equal(e, ref)
+    for c in ctxs:
+        c.close()
