@@ -13,10 +13,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(ROOT, "paper_1806_03761_gb300", "csrc")
 EMU = os.path.join(HERE, "host", "emu")
-# the units without tensor-core, static-scratch or server code
+# the units without tensor-core or static-scratch code
 UNITS = ["peps_api.cu", "peps_k_misc.cu"] + [
     "peps_k_%s_%s.cu" % (k, f) for k in ("eval", "sample", "vmc") for f in ("f64", "ff", "f32")] + [
-    "peps_k_%s_%s.cu" % (k, f) for k in ("corr", "multi") for f in ("f64", "ff")]
+    "peps_k_%s_%s.cu" % (k, f) for k in ("corr", "multi") for f in ("f64", "ff")] + ["peps_server.cu"]
 
 _LAUNCH = re.compile(r"(\b[A-Za-z_]\w*(?:<[^<>;]*>)?)\s*<<<([^>]*)>>>\s*\((.*?)\)\s*;", re.S)
 
@@ -38,7 +38,9 @@ def build(outdir, defines=(), sanitize=False):
         raise RuntimeError("no g++")
     os.makedirs(outdir, exist_ok=True)
     opt = ["-O1", "-g", "-fsanitize=address", "-fno-omit-frame-pointer"] if sanitize else ["-O2"]
-    flags = [gxx, "-std=c++20", "-ffp-contract=off", "-fPIC", "-pthread", "-w",
+    # -U_FORTIFY_SOURCE: the fibers switch stacks with _longjmp, which the
+    # fortified longjmp would refuse
+    flags = [gxx, "-std=c++20", "-ffp-contract=off", "-fPIC", "-pthread", "-w", "-U_FORTIFY_SOURCE",
              "-I", EMU, "-I", CSRC, "-I", os.path.join(ROOT, "include")] + opt + \
         ["-D%s" % d for d in defines]
     jobs = []

@@ -6,8 +6,8 @@
 // fibers of one host thread, resumed in turn; __syncthreads parks a fiber
 // until the whole block has arrived, __syncwarp and the warp shuffles until
 // its group of 32 has; __shared__ variables are function-local statics (one
-// block runs at a time, so one copy serves every block); atomics are plain
-// read-modify-writes (one host thread).
+// block runs at a time on a host thread, so one copy per host thread serves
+// every block); atomics are std::atomic_ref.
 // "Device" memory is host memory: cudaMalloc is malloc, every copy is
 // memcpy, streams are synchronous.  FP32 intrinsics are IEEE binary32
 // operations (the build uses -ffp-contract=off).
@@ -16,13 +16,21 @@
 // own attribute spellings
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cmath>
+#include <condition_variable>
 #include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <deque>
 #include <functional>
+#include <map>
+#include <mutex>
+#include <new>
 #include <string>
+#include <thread>
+#include <unordered_map>
 #include <vector>
 
 // ---- qualifiers -------------------------------------------------------------
@@ -31,7 +39,7 @@
 #define __host__
 #define __forceinline__ inline
 #define __noinline__ __attribute__((noinline))
-#define __shared__ static
+#define __shared__ static thread_local
 #define __restrict__ __restrict
 #define __align__(n) alignas(n)
 #define __launch_bounds__(...)
@@ -42,11 +50,13 @@ struct dim3 {
   unsigned x, y, z;
   dim3(unsigned a = 1, unsigned b = 1, unsigned c = 1) : x(a), y(b), z(c) {}
 };
-// set by the scheduler before it resumes a thread (one host thread runs all)
-extern uint3 threadIdx;
-extern uint3 blockIdx;
-extern dim3 blockDim;
-extern dim3 gridDim;
+// set by the scheduler before it resumes a thread; per host thread, so that
+// launches from different host threads (the serving loop's worker) do not
+// share them
+extern thread_local uint3 threadIdx;
+extern thread_local uint3 blockIdx;
+extern thread_local dim3 blockDim;
+extern thread_local dim3 gridDim;
 
 // ---- synchronisation --------------------------------------------------------
 // The threads of a block are fibers of one host thread; a barrier parks the
@@ -56,10 +66,10 @@ struct EmuBarrier {
   int count, n;
 };
 void emu_wait(EmuBarrier& b);
-extern EmuBarrier emu_block_bar;
-extern EmuBarrier emu_warp_bar[32];
-extern uint64_t emu_slot[32][32];  // per-warp shuffle exchange
-extern int emu_acc;
+extern thread_local EmuBarrier emu_block_bar;
+extern thread_local EmuBarrier emu_warp_bar[32];
+extern thread_local uint64_t emu_slot[32][32];  // per-warp shuffle exchange
+extern thread_local int emu_acc;
 
 inline void __syncthreads() { emu_wait(emu_block_bar); }
 inline void __syncwarp(unsigned = 0xffffffffu) { emu_wait(emu_warp_bar[threadIdx.x / 32]); }
@@ -87,6 +97,7 @@ inline T __shfl_xor_sync(unsigned, T v, int o) {
 }
 
 // ---- atomics and clocks -----------------------------------------------------
+// (atomic also across host threads: two launches may share a flag word)
 inline int atomicOr(int* p, int v) { return std::atomic_ref<int>(*p).fetch_or(v); }
 inline int atomicAdd(int* p, int v) { return std::atomic_ref<int>(*p).fetch_add(v); }
 inline unsigned long long atomicAdd(unsigned long long* p, unsigned long long v) {
@@ -111,6 +122,8 @@ enum : int {
   cudaErrorInvalidDevice = 101, cudaErrorNotReady = 600
 };
 typedef void* cudaStream_t;
+typedef void* cudaEvent_t;
+enum { cudaStreamNonBlocking = 1, cudaEventDisableTiming = 2 };
 enum cudaMemcpyKind {
   cudaMemcpyHostToHost = 0, cudaMemcpyHostToDevice = 1, cudaMemcpyDeviceToHost = 2,
   cudaMemcpyDeviceToDevice = 3, cudaMemcpyDefault = 4
@@ -142,6 +155,31 @@ inline cudaError_t cudaMemsetAsync(void* d, int v, size_t n, cudaStream_t = null
   return cudaMemset(d, v, n);
 }
 inline cudaError_t cudaStreamSynchronize(cudaStream_t) { return cudaSuccess; }
+// streams and events: every operation is complete when its call returns
+inline cudaError_t cudaStreamCreateWithFlags(cudaStream_t* s, unsigned) {
+  *s = reinterpret_cast<cudaStream_t>(new char(0));
+  return cudaSuccess;
+}
+inline cudaError_t cudaStreamDestroy(cudaStream_t s) { delete static_cast<char*>(s); return cudaSuccess; }
+inline cudaError_t cudaEventCreateWithFlags(cudaEvent_t* e, unsigned) {
+  *e = reinterpret_cast<cudaEvent_t>(new char(0));
+  return cudaSuccess;
+}
+inline cudaError_t cudaEventDestroy(cudaEvent_t e) { delete static_cast<char*>(e); return cudaSuccess; }
+inline cudaError_t cudaEventRecord(cudaEvent_t, cudaStream_t = nullptr) { return cudaSuccess; }
+inline cudaError_t cudaEventQuery(cudaEvent_t) { return cudaSuccess; }
+inline cudaError_t cudaMallocAsync(void** p, size_t n, cudaStream_t) { return cudaMalloc(p, n); }
+inline cudaError_t cudaFreeAsync(void* p, cudaStream_t) { return cudaFree(p); }
+// the emulated device's memory (the serving loop's default budget is 90 % of
+// the free part)
+#ifndef EMU_MEM_BYTES
+#define EMU_MEM_BYTES (8ull << 30)
+#endif
+inline cudaError_t cudaMemGetInfo(size_t* free_b, size_t* total_b) {
+  *free_b = EMU_MEM_BYTES;
+  *total_b = EMU_MEM_BYTES;
+  return cudaSuccess;
+}
 inline cudaError_t cudaGetLastError() { return cudaSuccess; }
 inline const char* cudaGetErrorString(cudaError_t) { return "emulated CUDA error"; }
 inline cudaError_t cudaGetDevice(int* d) { *d = 0; return cudaSuccess; }

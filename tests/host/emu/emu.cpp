@@ -1,5 +1,7 @@
 // Launch machinery of the host emulation (see cuda_runtime.h): the threads
-// of a block are ucontext fibers of the calling host thread.
+// of a block are ucontext fibers of the calling host thread (all state is
+// per host thread, so launches from several host threads are independent).
+#include <setjmp.h>
 #include <ucontext.h>
 
 #include <cstdio>
@@ -7,32 +9,37 @@
 
 #include "cuda_runtime.h"
 
-uint3 threadIdx;
-uint3 blockIdx;
-dim3 blockDim;
-dim3 gridDim;
-EmuBarrier emu_block_bar;
-EmuBarrier emu_warp_bar[32];
-uint64_t emu_slot[32][32];
-int emu_acc;
+thread_local uint3 threadIdx;
+thread_local uint3 blockIdx;
+thread_local dim3 blockDim;
+thread_local dim3 gridDim;
+thread_local EmuBarrier emu_block_bar;
+thread_local EmuBarrier emu_warp_bar[32];
+thread_local uint64_t emu_slot[32][32];
+thread_local int emu_acc;
 
 namespace {
+// A fiber starts on its own stack through setcontext (once); afterwards the
+// fibers and the scheduler switch with _setjmp/_longjmp, which, unlike
+// swapcontext, make no signal-mask system call.
 struct Fiber {
   ucontext_t ctx;
+  jmp_buf jb;
+  bool started;
   const long* wait_on;  // generation counter this fiber waits to change
   long wait_gen;
   bool done;
 };
-ucontext_t g_sched;
-std::vector<Fiber> g_fibers;
-int g_cur;
-const std::function<void()>* g_body;
+thread_local jmp_buf g_sched;
+thread_local std::vector<Fiber> g_fibers;
+thread_local int g_cur;
+thread_local const std::function<void()>* g_body;
 constexpr size_t kStack = 256 * 1024;
 
 void fiber_entry() {
   (*g_body)();
   g_fibers[g_cur].done = true;
-  swapcontext(&g_fibers[g_cur].ctx, &g_sched);
+  _longjmp(g_sched, 1);
 }
 }  // namespace
 
@@ -46,7 +53,7 @@ void emu_wait(EmuBarrier& b) {
   Fiber& f = g_fibers[g_cur];
   f.wait_on = &b.gen;
   f.wait_gen = g;
-  swapcontext(&f.ctx, &g_sched);
+  if (!_setjmp(f.jb)) _longjmp(g_sched, 1);
 }
 
 void emu_launch(dim3 grid, dim3 block, const std::function<void()>& body) {
@@ -82,7 +89,13 @@ void emu_launch(dim3 grid, dim3 block, const std::function<void()>& body) {
         f.wait_on = nullptr;
         g_cur = (int)t;
         threadIdx = uint3{t, 0, 0};
-        swapcontext(&g_sched, &f.ctx);
+        if (!_setjmp(g_sched)) {
+          if (!f.started) {
+            f.started = true;
+            setcontext(&f.ctx);
+          }
+          _longjmp(f.jb, 1);
+        }
         progress = true;
         if (f.done) --alive;
       }

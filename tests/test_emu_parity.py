@@ -102,7 +102,7 @@ class Ctx:
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-@pytest.mark.parametrize("L,D,Dc", [(3, 2, 8), (4, 3, 4)])
+@pytest.mark.parametrize("L,D,Dc", [(3, 2, 8), (4, 3, 4), (6, 4, 8)])
 def test_evaluation_matches_the_oracle(lib, prec, L, D, Dc):
     A = make_peps(L, D, seed=40 + L)
     spins = random_sz0_configs(L, 3, seed=41 + L)
@@ -135,12 +135,12 @@ def test_evaluation_matches_the_oracle(lib, prec, L, D, Dc):
     assert abs(r["sum_e"][0] - ref["e_loc"].sum()) <= tol * max(1, abs(ref["e_loc"].sum()))
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_sampler_bit_exact(lib, prec):
+@pytest.mark.parametrize("prec,L,D,Dc", [("fp64", 4, 3, 4), ("mixed", 4, 3, 4), ("fp64", 6, 4, 8)])
+def test_sampler_bit_exact(lib, prec, L, D, Dc):
     """Metropolis chains (Fisher-Yates starts, exchange moves, Philox draws)
     equal the oracle's configurations and acceptance counts bit for bit, and
-    resume from their final states."""
-    L, D, Dc = 4, 3, 4
+    resume from their final states (6x6 D=4 Dc=8: multi-panel QR and
+    blocked bidiagonalisation in every compression)."""
     A = make_peps(L, D, seed=1)
     c = Ctx(lib, L, D, Dc, prec, slots=2)
     c.set_tensors(A)
@@ -255,3 +255,89 @@ def test_multi_shape_launch_equals_each_context(lib):
         assert np.array_equal(e, ref)
     for c in ctxs:
         c.close()
+
+
+# ---------------------------------------------------------------------------
+# the serving loop (peps_server_*: host C++ worker and reaper threads) on the
+# emulated device: every stream operation completes when issued
+# ---------------------------------------------------------------------------
+SERVE_JOBS = [(4, 2, 4, "fp64", 2, 11), (4, 3, 4, "mixed", 2, 12), (3, 2, 8, "fp64", 2, 13)]
+
+
+class Server:
+    def __init__(self, lib, budget=0, slots=2):
+        self.lib, self.h, self.keep = lib, ctypes.c_void_p(), {}
+        assert lib.peps_server_create(budget, slots, ctypes.byref(self.h)) == 0
+
+    def submit(self, L, D, Dc, prec, B, seed):
+        from paper_1806_03761_gb300 import _lib as Bl
+        A = np.ascontiguousarray(make_peps(L, D, seed))
+        S = np.ascontiguousarray(random_sz0_configs(L, B, seed + 100))
+        out = dict(e_loc=np.zeros(B), log_abs=np.zeros(B), sign=np.zeros(B, np.int8))
+        code = {"fp64": Bl.PEPS_FP64, "mixed": Bl.PEPS_MIXED}[prec]
+        job = Bl.PepsJob(Bl.PepsShape(L, D, Dc, 1.0, 0.5, code), _p(A).value, _p(S).value, B,
+                         _p(out["e_loc"]).value, _p(out["log_abs"]).value, _p(out["sign"]).value)
+        jid = ctypes.c_int64(0)
+        rc = self.lib.peps_server_submit(self.h, ctypes.byref(job), ctypes.byref(jid))
+        if rc != 0:
+            return rc
+        self.keep[jid.value] = (A, S, out)
+        return jid.value
+
+    def wait(self, jid):
+        from paper_1806_03761_gb300 import _lib as Bl
+        st = Bl.PepsJobStats()
+        rc = self.lib.peps_server_wait(self.h, jid, 0.0, ctypes.byref(st))
+        A, S, out = self.keep.pop(jid)
+        return dict(out, A=A, S=S, status=rc, admit_s=st.admit_s, done_s=st.done_s,
+                    footprint=st.footprint_bytes)
+
+    def close(self):
+        self.lib.peps_server_destroy(self.h)
+
+
+def test_server_mix_equals_alone_and_the_oracle(lib):
+    srv = Server(lib)
+    alone = [srv.wait(srv.submit(*j)) for j in SERVE_JOBS]
+    ids = [srv.submit(*j) for j in SERVE_JOBS]
+    mixed = [srv.wait(i) for i in ids]
+    srv.close()
+    for job, a, m in zip(SERVE_JOBS, alone, mixed):
+        assert a["status"] == 0 and m["status"] == 0
+        for k in ("e_loc", "log_abs", "sign"):
+            assert np.array_equal(a[k], m[k]), (job, k)
+        L, D, Dc, prec = job[:4]
+        ref = oracle.evaluate_batch(m["A"], m["S"], L, Dc)
+        assert np.array_equal(m["sign"], ref["sign"].astype(np.int8))
+        assert np.max(np.abs(m["e_loc"] - ref["e_loc"]) / np.maximum(1, np.abs(ref["e_loc"]))) <= TOL[prec]
+
+
+def test_server_budget_gates_admission_and_refuses(lib):
+    from paper_1806_03761_gb300 import _lib as Bl
+    job = SERVE_JOBS[0]
+    probe = Server(lib)
+    fp = probe.wait(probe.submit(*job))["footprint"]
+    probe.close()
+    assert fp > 0
+    srv = Server(lib, budget=int(1.5 * fp))  # one such job at a time
+    res = [srv.wait(i) for i in [srv.submit(*job) for _ in range(3)]]
+    assert srv.submit(4, 2, 200, "fp64", 2, 1) == Bl.PEPS_EINVAL   # Dc * D > 256
+    srv.close()
+    for k in range(1, 3):
+        assert res[k]["admit_s"] >= res[k - 1]["done_s"] - 1e-6
+        assert np.array_equal(res[k]["e_loc"], res[0]["e_loc"])
+    small = Server(lib, budget=fp // 2)
+    assert small.submit(*job) == Bl.PEPS_ENOMEM  # alone larger than the budget
+    small.close()
+
+
+def test_server_eviction_under_a_tight_budget(lib):
+    jobs = [SERVE_JOBS[0], SERVE_JOBS[2], SERVE_JOBS[0], SERVE_JOBS[2]]
+    probe = Server(lib)
+    alone = [probe.wait(probe.submit(*j)) for j in jobs]
+    probe.close()
+    srv = Server(lib, budget=int(1.2 * max(a["footprint"] for a in alone)))
+    res = [srv.wait(i) for i in [srv.submit(*j) for j in jobs]]
+    srv.close()
+    for a, r in zip(alone, res):
+        assert r["status"] == 0 and np.array_equal(a["e_loc"], r["e_loc"])
