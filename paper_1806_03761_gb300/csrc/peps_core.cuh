@@ -420,6 +420,16 @@ __device__ void householder_r_unblocked(R* X, int m, int n, R* Rout, R* sh) {
 #endif
 #define PEPS_QR_ROWS 896
 
+// The factorisations' two inline-PTX statements, as macros that a host build
+// of the kernels may define otherwise: an L1 prefetch of a global address,
+// and the named barrier of warp pair p (barrier 1 + p, 64 threads).
+#ifndef PEPS_PREFETCH_L1
+#define PEPS_PREFETCH_L1(ptr) asm volatile("prefetch.global.L1 [%0];" ::"l"(ptr))
+#endif
+#ifndef PEPS_PAIR_SYNC
+#define PEPS_PAIR_SYNC(p) asm volatile("bar.sync %0, 64;" ::"r"(1 + (p)) : "memory")
+#endif
+
 // PEPS_QR_ACC=1 (default): the trailing update's warp reductions merge the
 // lanes' compensated accumulators directly, and x - V w' is one compensated
 // accumulation per element (float-float: fewer FP32 operations at the same
@@ -455,7 +465,7 @@ __device__ __forceinline__ void qr_trailing(R* X, int m, int n, int k0, int mr, 
     if (c + nw < n) {
       const R* xn = x + (int64_t)nw * m;
       for (int i = lane * (128 / (int)sizeof(R)); i < mr; i += PEPS_WARP * (128 / (int)sizeof(R)))
-        asm volatile("prefetch.global.L1 [%0];" ::"l"(xn + i));
+        PEPS_PREFETCH_L1(xn + i);
     }
 #endif
     // w = V^T x
@@ -599,11 +609,11 @@ __device__ __forceinline__ void qr_trailing_pair(R* X, int m, int n, int k0, int
 #pragma unroll
       for (int s = 0; s < PEPS_QR_NB; ++s) mine[s] = wv[s];
     }
-    asm volatile("bar.sync %0, 64;" ::"r"(1 + pair) : "memory");
+    PEPS_PAIR_SYNC(pair);
     R tot[PEPS_QR_NB];
 #pragma unroll
     for (int s = 0; s < PEPS_QR_NB; ++s) tot[s] = lo[s] + hi[s];
-    asm volatile("bar.sync %0, 64;" ::"r"(1 + pair) : "memory");
+    PEPS_PAIR_SYNC(pair);
     R wt[PEPS_QR_NB];
 #pragma unroll
     for (int s = 0; s < PEPS_QR_NB; ++s) {

@@ -70,6 +70,12 @@ extern thread_local EmuBarrier emu_block_bar;
 extern thread_local EmuBarrier emu_warp_bar[32];
 extern thread_local uint64_t emu_slot[32][32];  // per-warp shuffle exchange
 extern thread_local int emu_acc;
+extern thread_local EmuBarrier emu_named_bar[16];  // bar.sync 1..15, 64 threads
+
+// the kernels' inline-PTX statements (peps_core.cuh): the L1 prefetch is a
+// hint (nothing to do), the warp pair's named barrier a 64-thread barrier
+#define PEPS_PREFETCH_L1(ptr) ((void)(ptr))
+#define PEPS_PAIR_SYNC(p) emu_wait(emu_named_bar[1 + (p)])
 
 inline void __syncthreads() { emu_wait(emu_block_bar); }
 inline void __syncwarp(unsigned = 0xffffffffu) { emu_wait(emu_warp_bar[threadIdx.x / 32]); }

@@ -17,6 +17,7 @@ thread_local EmuBarrier emu_block_bar;
 thread_local EmuBarrier emu_warp_bar[32];
 thread_local uint64_t emu_slot[32][32];
 thread_local int emu_acc;
+thread_local EmuBarrier emu_named_bar[16];
 
 namespace {
 // A fiber starts on its own stack through setcontext (once); afterwards the
@@ -67,6 +68,7 @@ void emu_launch(dim3 grid, dim3 block, const std::function<void()>& body) {
   for (unsigned x = 0; x < nb; ++x) {
     blockIdx = uint3{x, 0, 0};
     emu_block_bar = EmuBarrier{0, 0, (int)nt};
+    for (auto& nb16 : emu_named_bar) nb16 = EmuBarrier{0, 0, 64};
     for (unsigned w = 0; w < 32; ++w) {
       const int n = (w + 1) * 32 <= nt ? 32 : (w * 32 < nt ? (int)(nt - w * 32) : 0);
       emu_warp_bar[w] = EmuBarrier{0, 0, n};

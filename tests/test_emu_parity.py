@@ -341,3 +341,43 @@ def test_server_eviction_under_a_tight_budget(lib):
     srv.close()
     for a, r in zip(alone, res):
         assert r["status"] == 0 and np.array_equal(a["e_loc"], r["e_loc"])
+
+
+def test_tuned_variants_match_the_oracle(tmp_path_factory):
+    """Every library variant the tuning table selects, built for the host
+    with its knobs (the QR column prefetch, A'^T v one thread per column,
+    three blocks' register budget, the two-warp tall panels with their
+    named barriers): the evaluation matches the oracle, at 5x5 D=8 Dc=16
+    (1024-row QR panels: the tall path) for a variant with the tall-panel
+    pairing, else at 6x6 D=4 Dc=8."""
+    import json
+    from paper_1806_03761_gb300 import _lib as Bl
+    from paper_1806_03761_gb300 import build as B
+    table = json.load(open(B.TUNING))
+    seen = set()
+    for key, entry in sorted(table.items()):
+        knobs, prec = entry["choice"], entry["precision"]
+        tag = B.variant_tag(dict(B.DEFAULTS, **knobs), prec)
+        if tag in seen:
+            continue
+        seen.add(tag)
+        path = _emu.build(str(tmp_path_factory.mktemp("emu_variant")),
+                          defines=["%s=%d" % kv for kv in sorted(knobs.items())])
+        vlib = ctypes.CDLL(path)
+        for name, (res, args) in Bl._SIGS.items():
+            if hasattr(vlib, name):
+                fn = getattr(vlib, name)
+                fn.restype, fn.argtypes = res, args
+        L, D, Dc = (5, 8, 16) if knobs.get("PEPS_QR_TALL_PAIR") else (6, 4, 8)
+        A = make_peps(L, D, seed=6)
+        spins = random_sz0_configs(L, 2, seed=7)
+        c = Ctx(vlib, L, D, Dc, prec, slots=2)
+        c.set_tensors(A)
+        r = c.evaluate(spins)
+        assert c.status() == (0, 0), tag
+        c.close()
+        ref = oracle.evaluate_batch(A, spins, L, Dc)
+        assert np.array_equal(r["sign"], ref["sign"].astype(np.int8)), tag
+        assert np.max(np.abs(r["log_abs"] - ref["log_abs"])) <= TOL[prec], tag
+        assert np.max(np.abs(r["e_loc"] - ref["e_loc"]) / np.maximum(1, np.abs(ref["e_loc"]))) <= TOL[prec], tag
+    assert seen
