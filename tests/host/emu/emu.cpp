@@ -36,6 +36,19 @@ thread_local std::vector<Fiber> g_fibers;
 thread_local int g_cur;
 thread_local const std::function<void()>* g_body;
 constexpr size_t kStack = 256 * 1024;
+// order in which a pass resumes the runnable threads: 0 ascending, 1
+// descending, 2 a fresh pseudo-random permutation every pass.  A kernel
+// without data races (every read of another thread's write separated from it
+// by a barrier) gives the same results in every order.
+int g_order = 0;
+uint64_t g_seed = 1;
+
+uint64_t next_rand() {  // xorshift64
+  g_seed ^= g_seed << 13;
+  g_seed ^= g_seed >> 7;
+  g_seed ^= g_seed << 17;
+  return g_seed;
+}
 
 void fiber_entry() {
   (*g_body)();
@@ -83,9 +96,14 @@ void emu_launch(dim3 grid, dim3 block, const std::function<void()>& body) {
       makecontext(&f.ctx, fiber_entry, 0);
     }
     unsigned alive = nt;
+    std::vector<unsigned> order(nt);
+    for (unsigned t = 0; t < nt; ++t) order[t] = g_order == 1 ? nt - 1 - t : t;
     while (alive > 0) {
       bool progress = false;
-      for (unsigned t = 0; t < nt; ++t) {
+      if (g_order == 2)
+        for (unsigned t = nt - 1; t > 0; --t) std::swap(order[t], order[next_rand() % (t + 1)]);
+      for (unsigned o = 0; o < nt; ++o) {
+        const unsigned t = order[o];
         Fiber& f = g_fibers[t];
         if (f.done || (f.wait_on && *f.wait_on == f.wait_gen)) continue;
         f.wait_on = nullptr;
@@ -108,4 +126,10 @@ void emu_launch(dim3 grid, dim3 block, const std::function<void()>& body) {
       }
     }
   }
+}
+
+// the schedule of later launches (see g_order); seed for order 2
+extern "C" void emu_set_schedule(int order, unsigned long long seed) {
+  g_order = order;
+  g_seed = seed ? seed : 1;
 }

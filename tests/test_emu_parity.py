@@ -381,3 +381,63 @@ def test_tuned_variants_match_the_oracle(tmp_path_factory):
         assert np.max(np.abs(r["log_abs"] - ref["log_abs"])) <= TOL[prec], tag
         assert np.max(np.abs(r["e_loc"] - ref["e_loc"]) / np.maximum(1, np.abs(ref["e_loc"]))) <= TOL[prec], tag
     assert seen
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_no_data_race_between_barriers(lib, prec):
+    """Race check: the emulation resumes a block's threads in ascending,
+    descending and pseudo-random orders between barriers; a read of another
+    thread's write not separated from it by a barrier (__syncthreads,
+    __syncwarp, a shuffle, a named barrier) would see a different value in
+    some order.  Evaluation, the fused VMC step, sampling and correlations
+    give the same bits in every order."""
+    from oracle import correlations as oc
+    L, D, Dc = 4, 3, 4
+    A = make_peps(L, D, seed=90)
+    spins = np.ascontiguousarray(random_sz0_configs(L, 3, seed=91))
+    src = np.array([oc.centre_site(L), 3], np.int32)
+    lib.emu_set_schedule.argtypes = [ctypes.c_int, ctypes.c_ulonglong]
+    runs = []
+    try:
+        for order, seed in ((0, 1), (1, 1), (2, 7), (2, 12345)):
+            lib.emu_set_schedule(order, seed)
+            c = Ctx(lib, L, D, Dc, prec, slots=2)
+            c.set_tensors(A)
+            ev = c.evaluate(spins)
+            state = spins.copy()
+            v = c.vmc_step(5, state, 2)
+            out, acc = c.sample(9, 2, 1, 1, 1)
+            ss = np.zeros((3, 2, L * L))
+            assert lib.peps_correlations(c.h, _p(spins), 3, 2, _p(src), _p(ss), None, None) == 0
+            assert c.status() == (0, 0)
+            c.close()
+            runs.append([ev[k] for k in sorted(ev)] + [v[k] for k in sorted(v)] + [state, out, acc, ss])
+    finally:
+        lib.emu_set_schedule(0, 1)
+    for r in runs[1:]:
+        for a, b in zip(runs[0], r):
+            assert np.array_equal(a, b)
+
+
+def test_the_race_check_sees_a_planted_race(tmp_path):
+    """The schedule orders of the race check expose a read of another
+    thread's write with no barrier between them (a planted race), and agree
+    once the barrier is there."""
+    import os
+    import subprocess
+    out_so = str(tmp_path / "planted.so")
+    subprocess.run(["g++", "-std=c++20", "-O1", "-fPIC", "-shared", "-pthread", "-U_FORTIFY_SOURCE",
+                    "-I", _emu.EMU, os.path.join(_emu.EMU, "planted_race.cpp"),
+                    os.path.join(_emu.EMU, "emu.cpp"), "-o", out_so], check=True)
+    p = ctypes.CDLL(out_so)
+    p.emu_set_schedule.argtypes = [ctypes.c_int, ctypes.c_ulonglong]
+    res = {}
+    for barrier in (0, 1):
+        for order in (0, 1):
+            p.emu_set_schedule(order, 1)
+            o = np.zeros(64, np.int32)
+            p.planted_race(_p(o), barrier)
+            res[barrier, order] = o
+    assert not np.array_equal(res[0, 0], res[0, 1])
+    assert np.array_equal(res[1, 0], res[1, 1])
+    assert np.array_equal(res[1, 0], (np.arange(64) + 1) % 64 + 1)
