@@ -368,9 +368,10 @@ def test_tuned_variants_match_the_oracle(tmp_path_factory):
             if hasattr(vlib, name):
                 fn = getattr(vlib, name)
                 fn.restype, fn.argtypes = res, args
-        L, D, Dc = (5, 8, 16) if knobs.get("PEPS_QR_TALL_PAIR") else (6, 4, 8)
+        tall = bool(knobs.get("PEPS_QR_TALL_PAIR"))
+        L, D, Dc = (5, 8, 16) if tall else (6, 4, 8)
         A = make_peps(L, D, seed=6)
-        spins = random_sz0_configs(L, 2, seed=7)
+        spins = random_sz0_configs(L, 1 if tall else 2, seed=7)
         c = Ctx(vlib, L, D, Dc, prec, slots=2)
         c.set_tensors(A)
         r = c.evaluate(spins)
@@ -399,7 +400,7 @@ def test_no_data_race_between_barriers(lib, prec):
     lib.emu_set_schedule.argtypes = [ctypes.c_int, ctypes.c_ulonglong]
     runs = []
     try:
-        for order, seed in ((0, 1), (1, 1), (2, 7), (2, 12345)):
+        for order, seed in ((0, 1), (1, 1), (2, 7)):
             lib.emu_set_schedule(order, seed)
             c = Ctx(lib, L, D, Dc, prec, slots=2)
             c.set_tensors(A)
