@@ -29,7 +29,7 @@ def rewrite(src):
     return _LAUNCH.sub(sub, src)
 
 
-def build(outdir, defines=(), sanitize=False):
+def build(outdir, defines=(), sanitize=False, units=None):
     """Compile and link the emulated library into outdir; returns its path.
     sanitize: instrument it with AddressSanitizer (the process that loads it
     needs libasan preloaded)."""
@@ -44,7 +44,7 @@ def build(outdir, defines=(), sanitize=False):
              "-I", EMU, "-I", CSRC, "-I", os.path.join(ROOT, "include")] + opt + \
         ["-D%s" % d for d in defines]
     jobs = []
-    for u in UNITS:
+    for u in (units or UNITS):
         dst = os.path.join(outdir, u[:-3] + ".cpp")
         with open(os.path.join(CSRC, u)) as f:
             text = rewrite(f.read())
@@ -52,6 +52,8 @@ def build(outdir, defines=(), sanitize=False):
             f.write('#include "cuda_runtime.h"\n' + text)
         jobs.append((dst, dst[:-4] + ".o"))
     jobs.append((os.path.join(EMU, "emu.cpp"), os.path.join(outdir, "emu.o")))
+    if units:
+        jobs.append((os.path.join(EMU, "launch_stubs.cpp"), os.path.join(outdir, "launch_stubs.o")))
 
     def cc(j):
         r = subprocess.run(flags + ["-c", j[0], "-o", j[1]], capture_output=True, text=True)
@@ -99,6 +101,43 @@ def _asan_cases(lib_path):
         c.close()
 
 
+def count_ops(L, D, Dc, chains=1):
+    """FP32 operations per phase of one fused VMC step of the float-float
+    form (a build with the phase counters whose clock is the emulation's
+    count of FP32 rounding operations and fmaf), per chain, with the
+    kernels' own flop count (12 FP32 operations per float-float
+    multiply-add, 2 flops)."""
+    import ctypes
+    import sys
+    import tempfile
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import paper_1806_03761_gb300 as P
+    from paper_1806_03761_gb300 import _lib as B
+    from synth import make_peps, random_sz0_configs
+    from tests.test_emu_parity import Ctx
+    path = build(tempfile.mkdtemp(prefix="emu_ops"), defines=["EMU_COUNT_OPS", "PEPS_PHASES=1"],
+                 units=["peps_api.cu", "peps_k_misc.cu", "peps_k_vmc_ff.cu"])
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in B._SIGS.items():
+        if hasattr(lib, name):
+            fn = getattr(lib, name)
+            fn.restype, fn.argtypes = res, args
+    c = Ctx(lib, L, D, Dc, "mixed", slots=1)
+    c.set_tensors(make_peps(L, D, seed=3))
+    state = np.ascontiguousarray(random_sz0_configs(L, chains, seed=4))
+    n_ph = len(P.PepsContext.PHASES)
+    buf = (ctypes.c_uint64 * n_ph)()
+    n = ctypes.c_int32(0)
+    lib.peps_phase_cycles(c.h, buf, n_ph, ctypes.byref(n))
+    c.vmc_step(5, state, 2)
+    lib.peps_phase_cycles(c.h, buf, n_ph, ctypes.byref(n))
+    assert n.value == n_ph and c.status() == (0, 0)
+    c.close()
+    ops = {k: buf[i] / chains for i, k in enumerate(P.PepsContext.PHASES)}
+    return ops, P.flops_per_sample(L, D, Dc, "mixed", "vmc")
+
+
 if __name__ == "__main__":
     # python -m tests._emu --asan-check: the emulated kernels under
     # AddressSanitizer (any out-of-bounds access of a buffer aborts the run)
@@ -112,3 +151,13 @@ if __name__ == "__main__":
         r = subprocess.run([sys.executable, "-c", "from tests._emu import _asan_cases; _asan_cases(%r)" % path],
                            cwd=ROOT, env=env)
         sys.exit(r.returncode)
+    if sys.argv[1:2] == ["--count-ops"]:
+        # python -m tests._emu --count-ops L D Dc
+        L, D, Dc = (int(x) for x in sys.argv[2:5])
+        ops, model = count_ops(L, D, Dc)
+        total = ops["eval"] + ops["sweep"]
+        print("%dx%d D=%d Dc=%d, float-float, one fused VMC step per chain" % (L, L, D, Dc))
+        print("FP32 operations %.4g (%.4g flop-equivalent at 12 per multiply-add); "
+              "kernel flop count %.4g; ratio %.3f" % (total, total / 6, model, total / 6 / model))
+        for k, v in ops.items():
+            print("  %-9s %.4g  %5.1f %%" % (k, v, 100.0 * v / total))

@@ -109,16 +109,30 @@ inline int atomicAdd(int* p, int v) { return std::atomic_ref<int>(*p).fetch_add(
 inline unsigned long long atomicAdd(unsigned long long* p, unsigned long long v) {
   return std::atomic_ref<unsigned long long>(*p).fetch_add(v);
 }
+// EMU_COUNT_OPS: every FP32 rounding intrinsic and fmaf counts one operation
+// in emu_ops, and clock64() returns that count, so that a build with the
+// kernels' phase counters (PEPS_PHASES) reports FP32 operations per phase.
+extern thread_local unsigned long long emu_ops;
+#ifdef EMU_COUNT_OPS
+#define EMU_OP() (++emu_ops)
+inline long long clock64() { return (long long)emu_ops; }
+#else
+#define EMU_OP() ((void)0)
 inline long long clock64() { return 0; }
+#endif
 
 // ---- FP32 intrinsics ----------------------------------------------------------
-inline float __fadd_rn(float a, float b) { return a + b; }
-inline float __fsub_rn(float a, float b) { return a - b; }
-inline float __fmul_rn(float a, float b) { return a * b; }
-inline float __fdiv_rn(float a, float b) { return a / b; }
-inline float __fsqrt_rn(float a) { return std::sqrt(a); }
+inline float __fadd_rn(float a, float b) { EMU_OP(); return a + b; }
+inline float __fsub_rn(float a, float b) { EMU_OP(); return a - b; }
+inline float __fmul_rn(float a, float b) { EMU_OP(); return a * b; }
+inline float __fdiv_rn(float a, float b) { EMU_OP(); return a / b; }
+inline float __fsqrt_rn(float a) { EMU_OP(); return std::sqrt(a); }
 using std::fabs; using std::fma; using std::fmaf; using std::isfinite; using std::sqrt;
 using std::exp; using std::log; using std::frexp; using std::ldexp; using std::fmax; using std::fmin;
+#ifdef EMU_COUNT_OPS
+inline float emu_fmaf(float a, float b, float c) { EMU_OP(); return std::fmaf(a, b, c); }
+#define fmaf emu_fmaf
+#endif
 
 
 // ---- runtime ------------------------------------------------------------------
@@ -181,6 +195,14 @@ inline cudaError_t cudaFreeAsync(void* p, cudaStream_t) { return cudaFree(p); }
 #ifndef EMU_MEM_BYTES
 #define EMU_MEM_BYTES (8ull << 30)
 #endif
+template <class T> inline cudaError_t cudaMemcpyFromSymbol(void* dst, const T& sym, size_t n) {
+  std::memcpy(dst, &sym, n);
+  return cudaSuccess;
+}
+template <class T> inline cudaError_t cudaMemcpyToSymbol(T& sym, const void* src, size_t n) {
+  std::memcpy(&sym, src, n);
+  return cudaSuccess;
+}
 inline cudaError_t cudaMemGetInfo(size_t* free_b, size_t* total_b) {
   *free_b = EMU_MEM_BYTES;
   *total_b = EMU_MEM_BYTES;

@@ -18,6 +18,7 @@ thread_local EmuBarrier emu_warp_bar[32];
 thread_local uint64_t emu_slot[32][32];
 thread_local int emu_acc;
 thread_local EmuBarrier emu_named_bar[16];
+thread_local unsigned long long emu_ops;
 
 namespace {
 // A fiber starts on its own stack through setcontext (once); afterwards the
