@@ -101,7 +101,7 @@ def _asan_cases(lib_path):
         c.close()
 
 
-def count_ops(L, D, Dc, chains=1):
+def count_ops(L, D, Dc, chains=1, knobs=()):
     """FP32 operations per phase of one fused VMC step of the float-float
     form (a build with the phase counters whose clock is the emulation's
     count of FP32 rounding operations and fmaf), per chain, with the
@@ -116,7 +116,8 @@ def count_ops(L, D, Dc, chains=1):
     from paper_1806_03761_gb300 import _lib as B
     from synth import make_peps, random_sz0_configs
     from tests.test_emu_parity import Ctx
-    path = build(tempfile.mkdtemp(prefix="emu_ops"), defines=["EMU_COUNT_OPS", "PEPS_PHASES=1"],
+    path = build(tempfile.mkdtemp(prefix="emu_ops"),
+                 defines=["EMU_COUNT_OPS", "PEPS_PHASES=1"] + list(knobs),
                  units=["peps_api.cu", "peps_k_misc.cu", "peps_k_vmc_ff.cu"])
     lib = ctypes.CDLL(path)
     for name, (res, args) in B._SIGS.items():
@@ -152,11 +153,12 @@ if __name__ == "__main__":
                            cwd=ROOT, env=env)
         sys.exit(r.returncode)
     if sys.argv[1:2] == ["--count-ops"]:
-        # python -m tests._emu --count-ops L D Dc
+        # python -m tests._emu --count-ops L D Dc [KNOB=value ...]
         L, D, Dc = (int(x) for x in sys.argv[2:5])
-        ops, model = count_ops(L, D, Dc)
+        ops, model = count_ops(L, D, Dc, knobs=sys.argv[5:])
         total = ops["eval"] + ops["sweep"]
-        print("%dx%d D=%d Dc=%d, float-float, one fused VMC step per chain" % (L, L, D, Dc))
+        print("%dx%d D=%d Dc=%d, float-float, one fused VMC step per chain %s" % (L, L, D, Dc,
+                                                                             " ".join(sys.argv[5:])))
         print("FP32 operations %.4g (%.4g flop-equivalent at 12 per multiply-add); "
               "kernel flop count %.4g; ratio %.3f" % (total, total / 6, model, total / 6 / model))
         for k, v in ops.items():
