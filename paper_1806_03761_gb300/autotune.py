@@ -11,8 +11,9 @@ B-only digit), and the code paths PEPS_QR_PREFETCH (the next trailing column
 of the blocked QR prefetched into L1), PEPS_BIDIAG_TPC (A'^T v of the
 bidiagonalisation with one thread per column), PEPS_QR_TALL_PAIR (panels of
 897 to 2048 rows held in the registers of two warps per column),
-PEPS_CTR_PIPE (contraction operands loaded one reduction step ahead) and
-PEPS_QR_ACC (the QR's trailing update as compensated accumulations).  Search: the default, then one knob changed
+PEPS_CTR_PIPE (contraction operands loaded one reduction step ahead),
+PEPS_QR_ACC (the QR's trailing update as compensated accumulations) and
+PEPS_BIDIAG_FUSE (two barriers per bidiagonalisation step left out).  Search: the default, then one knob changed
 at a time (a coordinate step); every candidate library is built (the C ABI
 and the form's fused kernel recompiled, see build.py), then timed in its own
 process on one wave of chains of the shape: one warm-up VMC step and --steps
@@ -48,6 +49,7 @@ CANDIDATES = [
     {"PEPS_QR_PREFETCH": 1, "PEPS_BIDIAG_TPC": 1, "PEPS_QR_TALL_PAIR": 1, "PEPS_MINB": 3},
     {"PEPS_QR_PREFETCH": 1, "PEPS_BIDIAG_TPC": 1, "PEPS_MINB": 3, "PEPS_BA_FF": 2},
     {"PEPS_QR_PREFETCH": 1, "PEPS_BIDIAG_TPC": 1, "PEPS_MINB": 4},  # 4 blocks per SM, 64 registers
+    {"PEPS_QR_PREFETCH": 1, "PEPS_BIDIAG_TPC": 1, "PEPS_MINB": 3, "PEPS_BIDIAG_FUSE": 1},
 ]
 
 

@@ -60,7 +60,7 @@ def _compile(src, obj, verbose, extra=()):
 DEFAULTS = {"PEPS_QR_NB": 4, "PEPS_BA_FF": 4, "PEPS_BA_F64": 2, "PEPS_MINB": 2, "PEPS_NT": 256,
             "PEPS_QR_PREFETCH": 0, "PEPS_BIDIAG_TPC": 0, "PEPS_QR_TALL_PAIR": 0,
             "PEPS_BB_FF": 2, "PEPS_CTR_PIPE": 1, "PEPS_QR_ACC": 1,
-            "PEPS_PHASES": 0}
+            "PEPS_PHASES": 0, "PEPS_BIDIAG_FUSE": 0}
 FORMS = {"fp64": "f64", "mixed": "ff", "fp32": "f32"}
 TUNING = os.path.join(PKG, "tuning.json")
 

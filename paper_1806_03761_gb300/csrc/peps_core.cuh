@@ -412,6 +412,14 @@ __device__ void householder_r_unblocked(R* X, int m, int n, R* Rout, R* sh) {
 #ifndef PEPS_BIDIAG_TPC
 #define PEPS_BIDIAG_TPC 0
 #endif
+// PEPS_BIDIAG_FUSE=1: the bidiagonalisation leaves out two of its barriers
+// per step where each thread reads only what it wrote itself (the column
+// corrections of Y before the row of the current matrix; the row corrections
+// of W before the next step's column); the same operations in the same
+// order (bit-identical to PEPS_BIDIAG_FUSE=0).
+#ifndef PEPS_BIDIAG_FUSE
+#define PEPS_BIDIAG_FUSE 0
+#endif
 // Tall panels (more than PEPS_QR_ROWS rows, up to 2048): the trailing column
 // in the registers of two warps (qr_trailing_pair) instead of two streaming
 // passes of one warp.
@@ -1085,7 +1093,12 @@ __device__ void bidiag_blocked(R* A, int m, int p, int nb, R* d, R* e, R* tau, R
         }
         Yp[j * p + c] = y;
       }
+      // (d) reads Y[0..j] only in the columns c that this thread has just
+      // written (the same c = t + q nt): PEPS_BIDIAG_FUSE leaves out the
+      // barrier between the two loops
+#if !PEPS_BIDIAG_FUSE
       __syncthreads();
+#endif
       // (d) row k of the current matrix after the left reflector, columns
       //     k+1..p-1, into Up[:, j]
       for (int c = t; c < p; c += nt) {
@@ -1170,7 +1183,15 @@ __device__ void bidiag_blocked(R* A, int m, int p, int nb, R* d, R* e, R* tau, R
         }
         Wp[j * m + i] = x;
       }
+      // the next step's (a) reads W[.][i] only in the rows i that this
+      // thread has just written (the same i = t + q nt), and its other
+      // readers of W come after the barriers of (a) and (b):
+      // PEPS_BIDIAG_FUSE keeps this barrier only after the panel's last step
+#if PEPS_BIDIAG_FUSE
+      if (j + 1 == nbp) __syncthreads();
+#else
       __syncthreads();
+#endif
     }
     // the panel's update of the trailing matrix (rows, columns >= i0 + nbp)
     const int k1 = i0 + nbp;

@@ -442,3 +442,44 @@ def test_the_race_check_sees_a_planted_race(tmp_path):
     assert not np.array_equal(res[0, 0], res[0, 1])
     assert np.array_equal(res[1, 0], res[1, 1])
     assert np.array_equal(res[1, 0], (np.arange(64) + 1) % 64 + 1)
+
+
+def test_bidiag_without_the_two_barriers_is_bit_identical(tmp_path_factory):
+    """PEPS_BIDIAG_FUSE leaves out two barriers per bidiagonalisation step
+    where each thread reads only what it wrote itself: the fused step's
+    outputs equal those of the build with the barriers bit for bit, in every
+    resume order of the race check (both forms, 6x6 D=4 Dc=8; by hand also
+    4x4 D=6 Dc=24 and the 1024-row panels of 5x5 D=8 Dc=16)."""
+    from paper_1806_03761_gb300 import _lib as Bl
+
+    def load(defs):
+        lib = ctypes.CDLL(_emu.build(str(tmp_path_factory.mktemp("fuse")), defines=defs))
+        for name, (res, args) in Bl._SIGS.items():
+            if hasattr(lib, name):
+                fn = getattr(lib, name)
+                fn.restype, fn.argtypes = res, args
+        lib.emu_set_schedule.argtypes = [ctypes.c_int, ctypes.c_ulonglong]
+        return lib
+
+    base = load(["PEPS_BIDIAG_TPC=1"])
+    fuse = load(["PEPS_BIDIAG_TPC=1", "PEPS_BIDIAG_FUSE=1"])
+
+    def run(lib, L, D, Dc, prec, order):
+        lib.emu_set_schedule(order, 3)
+        try:
+            c = Ctx(lib, L, D, Dc, prec, slots=1)
+            c.set_tensors(make_peps(L, D, seed=L + D))
+            state = np.ascontiguousarray(random_sz0_configs(L, 1, seed=5))
+            v = c.vmc_step(3, state, 1)
+            assert c.status() == (0, 0)
+            c.close()
+        finally:
+            lib.emu_set_schedule(0, 1)
+        return [v[k] for k in sorted(v)] + [state]
+
+    for (L, D, Dc, prec) in [(6, 4, 8, "mixed"), (6, 4, 8, "fp64")]:
+        ref = run(base, L, D, Dc, prec, 0)
+        for order in ((0, 2) if prec == "mixed" else (0,)):
+            got = run(fuse, L, D, Dc, prec, order)
+            for a, b in zip(ref, got):
+                assert np.array_equal(a, b), (L, D, Dc, prec, order)
