@@ -483,3 +483,63 @@ def test_bidiag_without_the_two_barriers_is_bit_identical(tmp_path_factory):
             got = run(fuse, L, D, Dc, prec, order)
             for a, b in zip(ref, got):
                 assert np.array_equal(a, b), (L, D, Dc, prec, order)
+
+
+def test_abi_argument_checks(lib):
+    """The C ABI refuses invalid arguments with PEPS_EINVAL and a message
+    (peps_last_error), and accepts the empty batch: shapes out of range,
+    NULL buffers, calls before peps_set_tensors, bad counts and ranges."""
+    from paper_1806_03761_gb300 import _lib as Bl
+    E = Bl.PEPS_EINVAL
+    h = ctypes.c_void_p()
+    for (L, D, Dc, prec) in [(1, 2, 4, 0), (33, 2, 4, 0), (4, 0, 4, 0), (4, 9, 4, 0), (4, 2, 0, 0),
+                             (4, 8, 33, 0), (4, 2, 4, 7)]:
+        sh = Bl.PepsShape(L, D, Dc, 1.0, 0.5, prec)
+        assert lib.peps_create(ctypes.byref(sh), 0, ctypes.byref(h)) == E, (L, D, Dc, prec)
+    sh = Bl.PepsShape(4, 2, 4, float("nan"), 0.5, Bl.PEPS_FP64)
+    assert lib.peps_create(ctypes.byref(sh), 0, ctypes.byref(h)) == E
+    sh = Bl.PepsShape(4, 2, 4, 1.0, 0.5, Bl.PEPS_FP64)
+    assert lib.peps_create(ctypes.byref(sh), -1, ctypes.byref(h)) == E
+    assert lib.peps_workspace_bytes(ctypes.byref(sh), 3) > 0
+    c = Ctx(lib, 4, 2, 4, "fp64", slots=2)
+    L, N = 4, 16
+    sp = np.ascontiguousarray(random_sz0_configs(L, 2, seed=1))
+    e = np.zeros(2)
+    out = np.zeros((2, N), np.uint8)
+    # before peps_set_tensors
+    assert lib.peps_sample_batch(c.h, 1, 2, 0, 0, 1, 1, 1, _p(out), None, None, None) == E
+    assert b"set_tensors" in lib.peps_last_error(c.h)
+    c.set_tensors(make_peps(L, 2, seed=2))
+    assert lib.peps_sample_batch(c.h, 1, 2, 0, 0, 0, 1, 1, _p(out), None, None, None) == E  # n_thin
+    assert lib.peps_sample_batch(c.h, 1, 2, 1 << 32, 0, 1, 1, 1, _p(out), None, None, None) == E
+    assert lib.peps_sample_batch(c.h, 1, 2, 0, 0, 1, 1, 1, None, None, None, None) == E
+    assert lib.peps_sample_batch(c.h, 1, 0, 0, 0, 1, 1, 1, None, None, None, None) == 0  # empty
+    assert lib.peps_vmc_step(c.h, 1, 0, 0, 1, _p(out), _p(e), None, None, None, None, None, 0,
+                             None, None) == E
+    assert lib.peps_vmc_step(c.h, 1, 2, 0, 1, None, _p(e), None, None, None, None, None, 0,
+                             None, None) == E
+    assert lib.peps_local_energy(c.h, _p(sp), 2, None, None, None, None, None, None) == E
+    sd = np.zeros(N * 2 * 16)
+    se = np.zeros(1)
+    A = np.ascontiguousarray(make_peps(L, 2, seed=2))
+    assert lib.peps_grad_step(c.h, _p(sd), _p(sd), _p(se), 0, 0.1, 1, 1, _p(A), None) == E  # M
+    assert lib.peps_grad_step(c.h, _p(sd), _p(sd), _p(se), 4, float("inf"), 1, 1, _p(A), None) == E
+    assert lib.peps_grad_step(c.h, _p(sd), _p(sd), _p(se), 4, 0.1, 1, 1 << 32, _p(A), None) == E
+    assert lib.peps_grad_step(c.h, None, _p(sd), _p(se), 4, 0.1, 1, 1, _p(A), None) == E
+    ss = np.zeros((2, 1, N))
+    bad = np.array([N], np.int32)
+    assert lib.peps_correlations(c.h, _p(sp), 2, 1, _p(bad), _p(ss), None, None) == E
+    assert b"source" in lib.peps_last_error(c.h)
+    assert lib.peps_correlations(c.h, _p(sp), 2, 0, _p(bad), _p(ss), None, None) == E
+    assert lib.peps_correlations(c.h, _p(sp), -1, 1, _p(np.array([0], np.int32)), _p(ss), None,
+                                 None) == E
+    assert c.status() == (0, 0)
+    c.close()
+    sh32 = Bl.PepsShape(4, 2, 4, 1.0, 0.5, Bl.PEPS_FP32)
+    h32 = ctypes.c_void_p()
+    assert lib.peps_create(ctypes.byref(sh32), 1, ctypes.byref(h32)) == 0
+    A32 = np.ascontiguousarray(make_peps(4, 2, seed=2))
+    assert lib.peps_set_tensors(h32, _p(A32), None) == 0
+    assert lib.peps_correlations(h32, _p(sp), 2, 1, _p(np.array([0], np.int32)), _p(ss), None,
+                                 None) == E  # FP32 form
+    lib.peps_destroy(h32)
