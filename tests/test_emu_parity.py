@@ -543,3 +543,51 @@ def test_abi_argument_checks(lib):
     assert lib.peps_correlations(h32, _p(sp), 2, 1, _p(np.array([0], np.int32)), _p(ss), None,
                                  None) == E  # FP32 form
     lib.peps_destroy(h32)
+
+
+def test_counter_and_host_buffer_steps_equal_the_direct_step(lib):
+    """Two VMC steps with the sweep and GO step numbers in device counters
+    (peps_vmc_step_dc, peps_grad_step_dc, peps_counters_advance: the calls a
+    CUDA graph replays) and through the host-buffer entry point
+    (peps_vmc_step_host) equal the direct calls bit for bit: chain states,
+    energies, gradient sums and the updated tensors."""
+    from paper_1806_03761_gb300 import _lib as Bl
+    lib.peps_counters_advance.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32,
+                                          ctypes.c_void_p]
+    L, D, Dc, n = 4, 2, 4, 3
+    A0 = make_peps(L, D, seed=33)
+    start = np.ascontiguousarray(random_sz0_configs(L, n, seed=34))
+    runs = {}
+    for mode in ("direct", "counters", "host"):
+        c = Ctx(lib, L, D, Dc, "mixed", slots=2)
+        A = np.ascontiguousarray(A0.copy())
+        c.set_tensors(A)
+        state = start.copy()
+        cnt = np.array([7, 3], np.uint32)
+        rec = []
+        for step in range(2):
+            e = np.zeros(n)
+            sd, sde, se = c.sums()
+            if mode == "direct":
+                assert lib.peps_vmc_step(c.h, 11, n, 0, 7 + step, _p(state), _p(e), None, None, _p(sd),
+                                         _p(sde), _p(se), 0, None, None) == 0
+                assert lib.peps_grad_step(c.h, _p(sd), _p(sde), _p(se), n, 0.05, 11, 3 + step, _p(A),
+                                          None) == 0
+            elif mode == "counters":
+                assert lib.peps_vmc_step_dc(c.h, 11, n, 0, _p(cnt), _p(state), _p(e), None, None, _p(sd),
+                                            _p(sde), _p(se), 0, None, None) == 0
+                assert lib.peps_grad_step_dc(c.h, _p(sd), _p(sde), _p(se), n, 0.05, 11, _p(cnt), _p(A),
+                                             None) == 0
+                assert lib.peps_counters_advance(_p(cnt), 2, 1, None) == 0
+            else:
+                assert lib.peps_vmc_step_host(c.h, 11, n, 0, 7 + step, _p(state), _p(e), None, None, None,
+                                              _p(sd), _p(sde), _p(se), None) == 0
+                assert lib.peps_grad_step(c.h, _p(sd), _p(sde), _p(se), n, 0.05, 11, 3 + step, _p(A),
+                                          None) == 0
+            rec += [state.copy(), e, sd, sde, se, A.copy()]
+        assert c.status() == (0, 0)
+        c.close()
+        runs[mode] = rec
+    for mode in ("counters", "host"):
+        for a, b in zip(runs["direct"], runs[mode]):
+            assert np.array_equal(a, b), mode
