@@ -101,7 +101,7 @@ def _asan_cases(lib_path):
         c.close()
 
 
-def count_ops(L, D, Dc, chains=1, knobs=()):
+def count_ops(L, D, Dc, chains=1, knobs=(), what="EMU_COUNT_OPS"):
     """FP32 operations per phase of one fused VMC step of the float-float
     form (a build with the phase counters whose clock is the emulation's
     count of FP32 rounding operations and fmaf), per chain, with the
@@ -117,7 +117,7 @@ def count_ops(L, D, Dc, chains=1, knobs=()):
     from synth import make_peps, random_sz0_configs
     from tests.test_emu_parity import Ctx
     path = build(tempfile.mkdtemp(prefix="emu_ops"),
-                 defines=["EMU_COUNT_OPS", "PEPS_PHASES=1"] + list(knobs),
+                 defines=[what, "PEPS_PHASES=1"] + list(knobs),
                  units=["peps_api.cu", "peps_k_misc.cu", "peps_k_vmc_ff.cu"])
     lib = ctypes.CDLL(path)
     for name, (res, args) in B._SIGS.items():
@@ -156,10 +156,16 @@ if __name__ == "__main__":
         # python -m tests._emu --count-ops L D Dc [KNOB=value ...]
         L, D, Dc = (int(x) for x in sys.argv[2:5])
         ops, model = count_ops(L, D, Dc, knobs=sys.argv[5:])
+        bars, _ = count_ops(L, D, Dc, knobs=sys.argv[5:], what="EMU_COUNT_BARRIERS")
         total = ops["eval"] + ops["sweep"]
         print("%dx%d D=%d Dc=%d, float-float, one fused VMC step per chain %s" % (L, L, D, Dc,
                                                                              " ".join(sys.argv[5:])))
         print("FP32 operations %.4g (%.4g flop-equivalent at 12 per multiply-add); "
-              "kernel flop count %.4g; ratio %.3f" % (total, total / 6, model, total / 6 / model))
+              "kernel flop count %.4g; ratio %.3f; block barriers %d" %
+              (total, total / 6, model, total / 6 / model, bars["eval"] + bars["sweep"]))
+        print("  %-9s %11s %7s %10s %14s" % ("phase", "FP32 ops", "share", "barriers",
+                                              "ops/barrier"))
         for k, v in ops.items():
-            print("  %-9s %.4g  %5.1f %%" % (k, v, 100.0 * v / total))
+            b = bars[k]
+            print("  %-9s %11.4g %6.1f%% %10d %14.4g" % (k, v, 100.0 * v / total, b,
+                                                          v / b if b else float("nan")))

@@ -112,13 +112,20 @@ inline unsigned long long atomicAdd(unsigned long long* p, unsigned long long v)
 // EMU_COUNT_OPS: every FP32 rounding intrinsic and fmaf counts one operation
 // in emu_ops, and clock64() returns that count, so that a build with the
 // kernels' phase counters (PEPS_PHASES) reports FP32 operations per phase.
+// EMU_COUNT_BARRIERS instead: clock64() returns the number of completed
+// block-wide barriers (__syncthreads) of the host thread's launches.
 extern thread_local unsigned long long emu_ops;
+extern thread_local unsigned long long emu_block_barriers;
 #ifdef EMU_COUNT_OPS
 #define EMU_OP() (++emu_ops)
 inline long long clock64() { return (long long)emu_ops; }
 #else
 #define EMU_OP() ((void)0)
+#ifdef EMU_COUNT_BARRIERS
+inline long long clock64() { return (long long)emu_block_barriers; }
+#else
 inline long long clock64() { return 0; }
+#endif
 #endif
 
 // ---- FP32 intrinsics ----------------------------------------------------------

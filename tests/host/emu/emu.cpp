@@ -19,6 +19,7 @@ thread_local uint64_t emu_slot[32][32];
 thread_local int emu_acc;
 thread_local EmuBarrier emu_named_bar[16];
 thread_local unsigned long long emu_ops;
+thread_local unsigned long long emu_block_barriers;
 
 namespace {
 // A fiber starts on its own stack through setcontext (once); afterwards the
@@ -63,6 +64,7 @@ void emu_wait(EmuBarrier& b) {
   if (++b.count == b.n) {
     b.count = 0;
     ++b.gen;
+    if (&b == &emu_block_bar) ++emu_block_barriers;
     return;
   }
   Fiber& f = g_fibers[g_cur];
