@@ -591,3 +591,41 @@ def test_counter_and_host_buffer_steps_equal_the_direct_step(lib):
     for mode in ("counters", "host"):
         for a, b in zip(runs["direct"], runs[mode]):
             assert np.array_equal(a, b), mode
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_amplitudes_and_logderiv_entry_points(lib, prec):
+    """peps_amplitudes (row-0 strip against Dn_1) and peps_logderiv (Delta of
+    every site on its s_m slice, the sums with given energies, accumulate)
+    against the oracle and against peps_evaluate."""
+    L, D, Dc = 4, 3, 4
+    A = make_peps(L, D, seed=101)
+    spins = np.ascontiguousarray(random_sz0_configs(L, 3, seed=102))
+    N, D4, B = L * L, D ** 4, 3
+    tol = TOL[prec]
+    c = Ctx(lib, L, D, Dc, prec, slots=2)
+    c.set_tensors(A)
+    la, sg = np.zeros(B), np.zeros(B, np.int8)
+    assert lib.peps_amplitudes(c.h, _p(spins), B, _p(la), _p(sg), None) == 0
+    ref = oracle.evaluate_batch(A, spins, L, Dc, want_delta=True)
+    assert np.array_equal(sg, ref["sign"].astype(np.int8))
+    assert np.max(np.abs(la - ref["log_abs"])) <= tol
+    e = np.ascontiguousarray(ref["e_loc"])
+    delta = np.zeros((B, N, D4))
+    sd, sde, se = c.sums()
+    assert lib.peps_logderiv(c.h, _p(spins), B, _p(e), _p(delta), _p(sd), _p(sde), _p(se), 0,
+                             None) == 0
+    for b in range(B):
+        for m in range(N):
+            want = ref["delta"][b, m, spins[b][m]].reshape(-1)
+            assert np.max(np.abs(delta[b, m] - want)) <= tol * max(1.0, np.abs(want).max())
+    # accumulate = 1 adds a second pass to the sums
+    sd2, sde2, se2 = sd.copy(), sde.copy(), se.copy()
+    assert lib.peps_logderiv(c.h, _p(spins), B, _p(e), None, _p(sd2), _p(sde2), _p(se2), 1,
+                             None) == 0
+    assert np.allclose(sd2, 2 * sd, rtol=1e-12, atol=0) and np.allclose(sde2, 2 * sde, rtol=1e-12, atol=0)
+    assert se2[0] == 2 * se[0] and abs(se[0] - e.sum()) <= 1e-12 * max(1, abs(e.sum()))
+    ev = c.evaluate(spins)
+    assert np.array_equal(ev["log_abs"], la) and np.array_equal(ev["sign"], sg)
+    assert c.status() == (0, 0)
+    c.close()
